@@ -1,0 +1,227 @@
+"""Plain FP64 matrix-product-state simulator of one TE-PAI circuit (Sec. II.A).
+
+Open chain in natural site order. Site tensors are A_i[chi_{i-1}][2][chi_i]
+in mixed-canonical form with an explicit orthogonality centre.
+
+- A two-site gate on bond (i, i+1) moves the centre to site i (Householder
+  QR / LQ through numpy.linalg.qr) and forms theta = A_i A_{i+1}. It applies
+  the 4x4 gate and factorises theta by SVD (numpy.linalg.svd, LAPACK). It
+  keeps at most chi_max singular values, renormalises the kept ones to unit
+  norm, and leaves the centre on site i+1 (Sec. II.A, bond-dimension and
+  truncation paragraphs).
+- Truncation keeps the k largest singular values, with
+  k = max(1, min(chi_max, k_floor, k_cut, len(s))):
+    k_cut   = the smallest k with sum_{j>=k} s_j^2 <= cutoff * sum_j s_j^2;
+    k_floor = #{j : s_j > floor_rel * s_0}, which drops singular values that
+              are zero to working precision.
+- A single-site gate, and a pi-rotation of a bond term (a product of two
+  single-site Paulis), act on the physical index directly. A unitary on one
+  site keeps every canonical condition.
+- A gate on the ring bond (n-1, 0) is routed by swaps: site n-1 is swapped
+  left to position 1, the gate acts on chain bond (0, 1), and the site is
+  swapped back. Every swap is a two-site update with truncation.
+- <Z_i> is contracted with left and right environments. This makes no
+  canonical-form assumption.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import gates
+from .sampler import EV_B, EV_C, EV_T
+
+ZDIAG = np.array([1.0, -1.0])
+
+
+class MPS:
+    def __init__(self, tensors, centre: int):
+        self.A = [np.asarray(a, dtype=np.complex128) for a in tensors]
+        self.c = centre
+        self.stats = {"gate_updates": 0, "swap_updates": 0, "qr_moves": 0,
+                      "max_discarded": 0.0, "max_chi": 1}
+
+    @property
+    def n(self):
+        return len(self.A)
+
+    def bond_dims(self):
+        return [1] + [a.shape[2] for a in self.A[:-1]] + [1]
+
+
+def product_state(bits) -> MPS:
+    ts = []
+    for b in bits:
+        a = np.zeros((1, 2, 1), dtype=np.complex128)
+        a[0, int(b), 0] = 1.0
+        ts.append(a)
+    return MPS(ts, 0)
+
+
+def _move_right(m: MPS):
+    c = m.c
+    A = m.A[c]
+    chl, d, chr_ = A.shape
+    Q, R = np.linalg.qr(A.reshape(chl * d, chr_))
+    m.A[c] = Q.reshape(chl, d, Q.shape[1])
+    m.A[c + 1] = np.tensordot(R, m.A[c + 1], axes=(1, 0))
+    m.c = c + 1
+    m.stats["qr_moves"] += 1
+
+
+def _move_left(m: MPS):
+    c = m.c
+    A = m.A[c]
+    chl, d, chr_ = A.shape
+    # A = L Q with Q right-orthonormal rows: QR of A^H.
+    Q, R = np.linalg.qr(A.reshape(chl, d * chr_).conj().T)
+    m.A[c] = Q.conj().T.reshape(Q.shape[1], d, chr_)
+    m.A[c - 1] = np.tensordot(m.A[c - 1], R.conj().T, axes=(2, 0))
+    m.c = c - 1
+    m.stats["qr_moves"] += 1
+
+
+def move_centre(m: MPS, target: int):
+    while m.c < target:
+        _move_right(m)
+    while m.c > target:
+        _move_left(m)
+
+
+def canonicalize(tensors) -> MPS:
+    """Bring arbitrary site tensors to right-canonical form with the centre
+    on site 0, then normalise the state."""
+    m = MPS(tensors, len(tensors) - 1)
+    move_centre(m, 0)
+    m.A[0] = m.A[0] / np.linalg.norm(m.A[0])
+    m.stats["qr_moves"] = 0
+    return m
+
+
+def keep_count(s: np.ndarray, chi_max: int, cutoff: float, floor_rel: float) -> int:
+    if s.size == 0 or s[0] <= 0.0:
+        return 1
+    w = s.astype(np.float64) ** 2
+    tot = float(np.sum(w))
+    # tail[k] = sum_{j >= k} w_j, accumulated from the smallest value upward
+    tail = np.zeros(s.size + 1)
+    acc = 0.0
+    for j in range(s.size - 1, -1, -1):
+        acc += w[j]
+        tail[j] = acc
+    k_cut = s.size
+    for k in range(1, s.size + 1):
+        if tail[k] <= cutoff * tot:
+            k_cut = k
+            break
+    k_floor = int(np.count_nonzero(s > floor_rel * s[0]))
+    return max(1, min(chi_max, k_floor, k_cut, s.size))
+
+
+def apply_two(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float,
+              floor_rel: float, swap: bool = False):
+    """Two-site update on bond (i, i+1) with a 4x4 gate g (basis |s_i s_{i+1}>)."""
+    move_centre(m, i)
+    A, B = m.A[i], m.A[i + 1]
+    chl, chr_ = A.shape[0], B.shape[2]
+    th = np.tensordot(A, B, axes=(2, 0))                          # (chl,2,2,chr)
+    th = np.einsum('stuv,auvb->astb', g.reshape(2, 2, 2, 2), th)
+    M = th.reshape(chl * 2, 2 * chr_)
+    U, s, Vh = np.linalg.svd(M, full_matrices=False)
+    k = keep_count(s, chi_max, cutoff, floor_rel)
+    tot = float(np.sum(s.astype(np.float64) ** 2))
+    kept = s[:k]
+    disc = 0.0 if tot == 0.0 else float(np.sum(s[k:] ** 2)) / tot
+    kept = kept / np.sqrt(np.sum(kept ** 2))
+    m.A[i] = U[:, :k].reshape(chl, 2, k)
+    m.A[i + 1] = (kept[:, None] * Vh[:k, :]).reshape(k, 2, chr_)
+    m.c = i + 1
+    m.stats["swap_updates" if swap else "gate_updates"] += 1
+    m.stats["max_discarded"] = max(m.stats["max_discarded"], disc)
+    m.stats["max_chi"] = max(m.stats["max_chi"], k)
+
+
+def apply_one(m: MPS, i: int, u: np.ndarray):
+    m.A[i] = np.einsum('st,atb->asb', u, m.A[i])
+
+
+class GateCache:
+    """Gate matrices per (term, setting), built once from the gate module."""
+
+    def __init__(self, plan):
+        self.plan = plan
+        self.cache = {}
+
+    def get(self, k: int, v: int) -> np.ndarray:
+        key = (k, v)
+        if key not in self.cache:
+            t = self.plan.terms[k]
+            if v == EV_C:
+                self.cache[key] = gates.PAULI[t.pauli[0]]   # one factor per site
+            elif v == EV_B:
+                self.cache[key] = gates.rotation(t.pauli, self.plan.phi[k])
+            else:
+                self.cache[key] = gates.rotation(t.pauli, self.plan.theta[k])
+        return self.cache[key]
+
+
+def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
+                cutoff: float, floor_rel: float):
+    t = plan.terms[k]
+    g = cache.get(k, v)
+    if t.pauli == 'Z':
+        apply_one(m, t.a, g)
+        return
+    if v == EV_C:
+        # R_k(pi) = -i P (x) P: one Pauli on each site, global phase dropped
+        apply_one(m, t.a, g)
+        apply_one(m, t.b, g)
+        return
+    n = m.n
+    if t.b == t.a + 1:
+        apply_two(m, t.a, g, chi_max, cutoff, floor_rel)
+        return
+    # ring bond (n-1, 0): route site n-1 next to site 0 by swaps
+    assert t.a == n - 1 and t.b == 0
+    for p in range(n - 2, 0, -1):
+        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True)
+    # chain bond (0, 1) now holds (site 0, site n-1): reorder the gate basis
+    g01 = gates.SWAP @ g @ gates.SWAP
+    apply_two(m, 0, g01, chi_max, cutoff, floor_rel)
+    for p in range(1, n - 1):
+        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True)
+
+
+def expect_z(m: MPS) -> np.ndarray:
+    """<Z_i> / <psi|psi> for all sites by left and right environments."""
+    n = m.n
+    Lenv = [np.ones((1, 1), dtype=np.complex128)]
+    for i in range(n):
+        A = m.A[i]
+        Lenv.append(np.einsum('ab,asc,bsd->cd', Lenv[i], A.conj(), A))
+    Renv = [None] * (n + 1)
+    Renv[n] = np.ones((1, 1), dtype=np.complex128)
+    for i in range(n - 1, -1, -1):
+        A = m.A[i]
+        Renv[i] = np.einsum('asc,bsd,cd->ab', A.conj(), A, Renv[i + 1])
+    norm = Lenv[n][0, 0].real
+    out = np.zeros(n)
+    for i in range(n):
+        A = m.A[i]
+        out[i] = np.einsum('ab,asc,s,bsd,cd->', Lenv[i], A.conj(), ZDIAG, A,
+                           Renv[i + 1]).real / norm
+    return out
+
+
+def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
+               floor_rel: float = 1e-14) -> np.ndarray:
+    cache = GateCache(plan)
+    out = []
+    e = 0
+    ne = len(events)
+    for js in snap_steps:
+        while e < ne and events[e, 0] <= js:
+            apply_event(m, plan, cache, int(events[e, 1]), int(events[e, 2]),
+                        chi_max, cutoff, floor_rel)
+            e += 1
+        out.append(expect_z(m))
+    return np.array(out)

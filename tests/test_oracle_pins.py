@@ -1,0 +1,326 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(closed forms, invariants, brute force, library routines). CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize
+
+import workloads as W
+from oracle import enumerate as en
+from oracle import estimator, gates, planner, sampler
+from oracle import mps as M
+from oracle import run as R
+from oracle import statevector as sv
+from oracle.philox import philox4x64_scalar, philox4x64_vec
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- generator
+@pytest.mark.parametrize("key,ctr", [((0, 0), (1, 0, 0, 0)), ((5, 7), (3, 9, 0, 0)),
+                                     ((2**64 - 1, 12345), (2**63 + 5, 2**40, 7, 1))])
+def test_philox_matches_numpy_bitgenerator(key, ctr):
+    # numpy's Philox (4x64-10) increments the counter before producing a block
+    c = list(ctr)
+    c[0] = (c[0] - 1) % 2**64
+    ref = np.random.Philox(key=np.array(key, dtype=np.uint64),
+                          counter=np.array(c, dtype=np.uint64)).random_raw(4)
+    got = philox4x64_scalar(ctr, key)
+    assert [int(x) for x in ref] == list(got)
+    vec = philox4x64_vec(np.array([ctr[0]], np.uint64), np.array([ctr[1]], np.uint64),
+                         np.array([ctr[2]], np.uint64), np.array([ctr[3]], np.uint64), *key)
+    assert [int(v[0]) for v in vec] == list(got)
+
+
+# ---------------------------------------------------------------- gates
+@pytest.mark.parametrize("name", ["Z", "XX", "YY", "ZZ"])
+def test_rotation_closed_form(name):
+    P = gates.pauli_string(name)
+    for th in (0.3, -1.1, math.pi):
+        want = math.cos(th / 2) * np.eye(P.shape[0]) - 1j * math.sin(th / 2) * P
+        assert np.allclose(gates.rotation(name, th), want, atol=1e-14)
+
+
+# ---------------------------------------------------------------- P1: gammas
+def _rand_rho(d, rng):
+    a = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    r = a @ a.conj().T
+    return r / np.trace(r)
+
+
+@pytest.mark.parametrize("name", ["Z", "XX", "YY", "ZZ"])
+def test_pai_superoperator_identity(name):
+    """gamma_1 A + gamma_2 B + gamma_3 C = R(theta) as superoperators (App. A.3)."""
+    rng = np.random.default_rng(1)
+    d = 2 ** len(name)
+    for _ in range(20):
+        delta = rng.uniform(0.01, math.pi)
+        theta = rng.uniform(-delta, delta)
+        g1, g2, g3 = planner.gammas(theta, delta)
+        assert abs(g1 + g2 + g3 - 1.0) < 1e-14
+        rho = _rand_rho(d, rng)
+        Rt = gates.rotation(name, theta)
+        B = gates.rotation(name, math.copysign(delta, theta))
+        C = gates.rotation(name, math.pi)
+        lhs = g1 * rho + g2 * B @ rho @ B.conj().T + g3 * C @ rho @ C.conj().T
+        assert np.allclose(lhs, Rt @ rho @ Rt.conj().T, atol=1e-14)
+
+
+def test_pai_signs_and_norm_under_assumption():
+    for delta in (0.01, 0.5, 2.0):
+        for t in np.linspace(0, delta, 7):
+            g1, g2, g3 = planner.gammas(t, delta)
+            assert g1 >= -1e-15 and g2 >= 0 and g3 <= 1e-15
+            # ||gamma||_1 = 1 - 2 gamma_3 >= 1
+            assert abs(abs(g1) + abs(g2) + abs(g3) - (1 - 2 * g3)) < 1e-14
+
+
+# ---------------------------------------------------------------- golden: App. A.5
+def test_nu_inf_minimum_matches_paper_constants():
+    gold = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))
+    f = lambda d: (3 - math.cos(d)) / math.sin(d)
+    res = scipy.optimize.minimize_scalar(f, bounds=(0.05, 3.0), method="bounded",
+                                         options={"xatol": 1e-12})
+    assert abs(res.fun - gold["nu_inf_min_prefactor"]) < 1e-10
+    assert abs(res.x - gold["nu_inf_argmin_delta"]) < 1e-5
+    assert abs(res.x / math.pi - gold["nu_inf_argmin_delta_over_pi_printed"]) < 5e-4
+    # the oracle's nu_inf reproduces the bound with ||c||_1 T = 1
+    prob = W.uniform_chain(2, 0.2, periodic=False)        # 5 terms, ||c||_1 = 1
+    assert abs(planner.nu_infinity(prob, 1.0, gold["nu_inf_argmin_delta"])
+               - gold["nu_inf_min_prefactor"]) < 1e-12
+
+
+# ---------------------------------------------------------------- P2
+def test_delta_equals_theta_is_deterministic_trotter():
+    prob = W.uniform_chain(5, 0.5, periodic=True)
+    T, N = 1.0, 20
+    delta = 2 * 0.5 * T / N
+    plan = planner.make_plan(prob, T, N, delta)
+    assert np.allclose(plan.gam, [[0.0, 1.0, 0.0]] * len(plan.terms), atol=1e-15)
+    ev = sampler.sample_events(plan, 3, 11, N)
+    assert len(ev) == N * len(plan.terms) and np.all(ev[:, 2] == sampler.EV_B)
+    tplan = planner.make_plan(prob, T, N, delta, planner.TROTTER)
+    snaps = planner.snapshot_steps(N, 4)
+    z_tepai = sv.run_events(prob.init_bits, plan, ev, snaps)
+    z_trot = sv.run_events(prob.init_bits, tplan, sampler.sample_events(tplan, 0, 0, N), snaps)
+    assert np.max(np.abs(z_tepai - z_trot)) < 1e-12
+
+
+# ---------------------------------------------------------------- P3
+@pytest.mark.parametrize("n,N", [(2, 2), (3, 1)])
+def test_enumeration_is_unbiased(n, N):
+    """Statement 1: sum_l g_l <Z>_l over all settings = N-step Trotter value."""
+    prob = W.spin_ring(n, 1.0, seed=4, periodic=False)
+    T, delta = 0.2 * N, 0.5
+    plan = planner.make_plan(prob, T, N, delta)
+    assert planner.check_theta(plan)
+    z, gabs = en.enumerate_all(prob, plan, N)
+    tplan = planner.make_plan(prob, T, N, delta, planner.TROTTER)
+    z_trot = sv.run_events(prob.init_bits, tplan, sampler.sample_events(tplan, 0, 0, N), [N])[0]
+    assert np.max(np.abs(z - z_trot)) < 1e-12
+    assert abs(gabs - plan.gnorm_step ** N) < 1e-12
+
+
+# ---------------------------------------------------------------- P4
+def test_mean_gate_count_and_setting_frequencies():
+    prob = W.spin_ring(4, 1.0, seed=2)
+    T, N, delta = 1.0, 200, math.pi / 64
+    plan = planner.make_plan(prob, T, N, delta)
+    Ns = 3000
+    nus, ncs = [], []
+    for s in range(Ns):
+        ev = sampler.sample_events(plan, 7, s, N)
+        nus.append(len(ev))
+        ncs.append(int(np.count_nonzero(ev[:, 2] == sampler.EV_C)))
+    nus = np.array(nus, dtype=float)
+    mean_exact = N * plan.q.sum()
+    var_exact = N * np.sum(plan.q * (1 - plan.q))
+    assert abs(nus.mean() - mean_exact) < 4 * math.sqrt(var_exact / Ns)
+    assert abs(nus.var(ddof=1) / var_exact - 1) < 0.1
+    pc = N * np.sum(plan.q * plan.r)
+    assert abs(np.mean(ncs) - pc) < 4 * math.sqrt(pc / Ns) + 1e-9
+
+
+def test_expected_gate_count_tends_to_nu_inf():
+    prob, par, _ = W.config(2)
+    prev = None
+    for N in (2000, 8000, 32000):
+        plan = planner.make_plan(prob, par.T, N, par.delta)
+        rel = abs(planner.expected_nu(plan, N) - planner.nu_infinity(prob, par.T, par.delta)) \
+            / planner.nu_infinity(prob, par.T, par.delta)
+        if prev is not None:
+            assert rel < prev
+        prev = rel
+    assert prev < 1e-3
+
+
+# ---------------------------------------------------------------- P5
+def test_gnorm_tends_to_limit():
+    prob, par, _ = W.config(1)
+    lim = planner.gnorm_infinity(prob, par.T, par.delta)
+    rels = []
+    for N in (2000, 20000, 200000):
+        plan = planner.make_plan(prob, par.T, N, par.delta)
+        rels.append(abs(plan.gnorm_step ** N / lim - 1))
+    assert rels[0] > rels[1] > rels[2] and rels[2] < 5e-4
+
+
+# ---------------------------------------------------------------- P6
+@pytest.mark.parametrize("n", [5, 6])
+def test_untruncated_mps_equals_statevector(n):
+    prob = W.spin_ring(n, 1.0, seed=n)
+    T, N, delta = 1.0, 60, math.pi / 24
+    par = W.Params(T=T, n_steps=N, delta=delta, n_samples=3, chi_max=2 ** (n // 2),
+                   cutoff=0.0, n_snapshots=3, seed=5)
+    r1 = R.run(prob, par)
+    r2 = R.run(prob, par, use_statevector=True)
+    assert np.max(np.abs(r1["v"] - r2["v"])) < 1e-12
+    assert sum(st["swap_updates"] for st in r1["stats"]) > 0      # ring routing exercised
+
+
+# ---------------------------------------------------------------- P7
+def test_trotter_mode_mps_equals_statevector_and_conserves_magnetisation():
+    prob = W.spin_ring(8, 1.0, seed=0)
+    par = W.Params(T=1.0, n_steps=100, delta=math.pi / 256, n_samples=1, chi_max=16,
+                   cutoff=0.0, n_snapshots=5, variant=planner.TROTTER)
+    r1 = R.run(prob, par)
+    r2 = R.run(prob, par, use_statevector=True)
+    assert np.max(np.abs(r1["v"] - r2["v"])) < 1e-12
+    assert np.max(np.abs(r1["v"].sum(axis=2))) < 1e-12
+
+
+# ---------------------------------------------------------------- P8
+def test_tepai_mean_converges_to_trotter_and_exact():
+    prob = W.spin_ring(4, 1.0, seed=3)
+    T, N, delta = 1.0, 100, math.pi / 16
+    par = W.Params(T=T, n_steps=N, delta=delta, n_samples=1500, chi_max=4, cutoff=0.0,
+                   n_snapshots=4, seed=9)
+    r = R.run(prob, par, use_statevector=True)
+    tpar = W.Params(T=T, n_steps=N, delta=delta, n_samples=1, chi_max=4, cutoff=0.0,
+                    n_snapshots=4, variant=planner.TROTTER)
+    zt = R.run(prob, tpar, use_statevector=True)["v"][0]
+    dev = np.abs(r["mean"] - zt)
+    assert np.all(dev <= 4 * r["stderr"] + 1e-12)
+    # Statement 2: Var[v] <= 1 for the signed per-configuration values
+    assert np.all(np.var(r["sign"][:, :, None] * r["v"], axis=0) <= 1.0)
+    times = [T * j / N for j in r["snaps"]]
+    ze = sv.exact_z(prob, times)
+    # exact evolution within the statistical band plus the first-order Trotter error
+    assert np.all(np.abs(r["mean"] - ze) <= 4 * r["stderr"] + np.abs(zt - ze) + 1e-12)
+
+
+# ---------------------------------------------------------------- P9
+def test_two_site_heisenberg_closed_form():
+    J = 0.7
+    prob = W.Problem(n=2, periodic=False, Jx=np.array([J]), Jy=np.array([J]),
+                     Jz=np.array([J]), h=np.zeros(2), init_bits=np.array([0, 1], np.uint8))
+    ts = np.linspace(0, 2, 9)
+    z = sv.exact_z(prob, ts)
+    assert np.allclose(z[:, 0], np.cos(4 * J * ts), atol=1e-12)
+    assert np.allclose(z[:, 1], -np.cos(4 * J * ts), atol=1e-12)
+
+
+def test_single_qubit_rotation_expectation():
+    psi = sv.basis_state([0])
+    for phi in (0.2, 1.3, 2.9):
+        out = sv.apply_1(psi, gates.rotation('X', phi) if False else
+                         np.array([[math.cos(phi / 2), -1j * math.sin(phi / 2)],
+                                   [-1j * math.sin(phi / 2), math.cos(phi / 2)]]), 0)
+        assert abs(sv.expect_z(out)[0] - math.cos(phi)) < 1e-14
+
+
+# ---------------------------------------------------------------- P10
+def test_no_pi_variant():
+    prob = W.spin_ring(6, 1.0, seed=1)
+    T, N, delta = 1.0, 200, math.pi / 64
+    plan = planner.make_plan(prob, T, N, delta, planner.NO_PI)
+    assert abs(plan.gnorm_step - 1.0) < 1e-15
+    assert np.allclose(plan.q, np.abs(plan.theta) / delta, atol=1e-15)
+    for s in range(20):
+        ev = sampler.sample_events(plan, 1, s, N)
+        assert not np.any(ev[:, 2] == sampler.EV_C)
+        assert sampler.sign_after(ev, N) == 1
+
+
+# ---------------------------------------------------------------- estimator
+def test_neumaier_against_fsum():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(1000) * 1e16, rng.standard_normal(1000),
+                        -rng.standard_normal(1000) * 1e16])
+    rng.shuffle(x)
+    s, c = estimator.neumaier(x)
+    assert abs((s + c) - math.fsum(x)) <= 2.0
+
+
+def test_estimate_matches_plain_mean_and_std():
+    rng = np.random.default_rng(1)
+    v = rng.uniform(-1, 1, (500, 3, 4))
+    sg = rng.choice([-1, 1], (500, 3)).astype(np.int8)
+    gn = np.array([1.0, 1.5, 2.0])
+    mean, se, part = estimator.estimate(v, sg, gn)
+    x = sg[:, :, None] * v
+    assert np.allclose(mean, gn[:, None] * x.mean(axis=0), atol=1e-15)
+    assert np.allclose(se, gn[:, None] * x.std(axis=0, ddof=1) / math.sqrt(500), atol=1e-14)
+
+
+# ---------------------------------------------------------------- truncation / MPS
+def test_keep_count_brute_force():
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        s = np.sort(rng.exponential(1.0, rng.integers(1, 12)) ** 3)[::-1]
+        chi, cut = int(rng.integers(1, 10)), float(10.0 ** rng.uniform(-6, -0.5))
+        k = M.keep_count(s, chi, cut, 1e-14)
+        tot = np.sum(s ** 2)
+        ok = [kk for kk in range(1, len(s) + 1) if np.sum(s[kk:] ** 2) <= cut * tot]
+        assert k == max(1, min(chi, ok[0], len(s)))
+
+
+def test_truncated_update_discards_weight_per_eckart_young():
+    rng = np.random.default_rng(3)
+    ts, _ = W.random_mps_tensors(6, 8, seed=4)
+    m = M.canonicalize(ts)
+    before = M.expect_z(m)
+    M.move_centre(m, 2)
+    th = np.tensordot(m.A[2], m.A[3], axes=(2, 0))
+    g = gates.rotation('XX', 0.7)
+    th = np.einsum('stuv,auvb->astb', g.reshape(2, 2, 2, 2), th)
+    s = np.linalg.svd(th.reshape(th.shape[0] * 2, -1), compute_uv=False)
+    M.apply_two(m, 2, g, chi_max=3, cutoff=0.0, floor_rel=1e-14)
+    th2 = np.tensordot(m.A[2], m.A[3], axes=(2, 0)).reshape(th.shape[0] * 2, -1)
+    # rebuilt theta is the best rank-3 approximation, rescaled to unit norm
+    best = np.sum(s[:3] ** 2)
+    err = np.linalg.norm(th2 * math.sqrt(best) - th.reshape(th2.shape)) ** 2
+    assert abs(err - np.sum(s[3:] ** 2)) < 1e-12
+    assert m.stats["max_chi"] == 3
+    assert before.shape == (6,)
+
+
+def _dense_from_tensors(ts):
+    psi = ts[0]
+    for a in ts[1:]:
+        psi = np.tensordot(psi, a, axes=(psi.ndim - 1, 0))
+    return psi.reshape((2,) * len(ts))
+
+
+def test_canonicalize_and_measure_against_dense_contraction():
+    ts, _ = W.random_mps_tensors(7, 4, seed=8)
+    psi = _dense_from_tensors(ts)
+    want = sv.expect_z(psi)
+    m = M.canonicalize(ts)
+    assert np.allclose(M.expect_z(m), want, atol=1e-12)
+    # right-canonical: sum_s A^s A^s^dag = I for sites > 0
+    for a in m.A[1:]:
+        mat = a.reshape(a.shape[0], -1)
+        assert np.allclose(mat @ mat.conj().T, np.eye(a.shape[0]), atol=1e-12)
+
+
+def test_oracle_does_not_import_product_package():
+    here = os.path.join(os.path.dirname(os.path.dirname(__file__)), "oracle")
+    for f in os.listdir(here):
+        if f.endswith(".py"):
+            src = open(os.path.join(here, f)).read()
+            assert "paper_2604_13144_gb300" not in src
+            assert "import workloads" not in src

@@ -1,0 +1,139 @@
+"""Seeded synthetic inputs shared by the oracle-based tests, the CUDA parity
+tests and the benchmark.
+
+This module draws random numbers and lays out problem descriptions. It holds
+none of the method's arithmetic: no rotation angles, no quasi-probabilities,
+no gates and no tensor-network operations.
+
+The workloads are disordered spin rings of the form given in Sec. III,
+Eq. (spinRing): H = sum_k h_k Z_k + sum_bonds (Jx XX + Jy YY + Jz ZZ). The
+on-site fields are drawn uniformly from [-a, a]. The initial states are
+computational basis states such as |0101...>.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Problem:
+    """Hamiltonian and initial product state of one spin chain or ring."""
+    n: int
+    periodic: bool
+    Jx: np.ndarray          # one coupling per bond: n bonds (ring) or n-1 (chain)
+    Jy: np.ndarray
+    Jz: np.ndarray
+    h: np.ndarray           # one Z field per site
+    init_bits: np.ndarray   # uint8, one computational-basis bit per site
+
+    @property
+    def n_bonds(self) -> int:
+        return self.n if self.periodic else self.n - 1
+
+
+@dataclasses.dataclass
+class Params:
+    """Run parameters of one TE-PAI ensemble (names follow the paper)."""
+    T: float                  # total evolution time
+    n_steps: int              # N, Trotter steps of the sampled product formula
+    delta: float              # Delta, the fixed rotation angle of setting B
+    n_samples: int            # N_s
+    chi_max: int
+    cutoff: float             # discarded-weight fraction allowed per update
+    n_snapshots: int          # M, snapshots at j_m = m * run_steps / M
+    seed: int = 0             # circuit-sampler seed
+    sample_offset: int = 0    # global index of the first sample
+    variant: int = 0          # 0 unbiased TE-PAI, 1 no-pi TE-PAI, 2 Trotter
+    precision: int = 0        # 0 FP64, 1 mixed (FP32 tensors, FP64 bookkeeping)
+    run_steps: int = 0        # steps actually run (0 = all n_steps)
+    obs_sites: np.ndarray | None = None   # Z_i sites; None = all sites
+
+    def steps_run(self) -> int:
+        return self.n_steps if self.run_steps == 0 else self.run_steps
+
+
+def neel_bits(n: int) -> np.ndarray:
+    """|0101...>: site i holds bit (i mod 2)."""
+    return (np.arange(n) % 2).astype(np.uint8)
+
+
+def spin_ring(n: int, field_range: float, seed: int = 0, Jz: float = 1.0,
+              J: float = 1.0, periodic: bool = True) -> Problem:
+    """Disordered Heisenberg / XXZ ring with h_i ~ U[-a, a] drawn with
+    numpy's default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    h = rng.uniform(-field_range, field_range, n)
+    nb = n if periodic else n - 1
+    return Problem(n=n, periodic=periodic,
+                   Jx=np.full(nb, J), Jy=np.full(nb, J), Jz=np.full(nb, J * Jz),
+                   h=h.astype(np.float64), init_bits=neel_bits(n))
+
+
+def uniform_chain(n: int, c: float, periodic: bool = True) -> Problem:
+    """All couplings and fields equal to c (every |c_k| equal)."""
+    nb = n if periodic else n - 1
+    return Problem(n=n, periodic=periodic, Jx=np.full(nb, c), Jy=np.full(nb, c),
+                   Jz=np.full(nb, c), h=np.full(n, c), init_bits=neel_bits(n))
+
+
+def random_mps_tensors(n: int, chi: int, seed: int, dtype=np.complex128):
+    """Gaussian random site tensors A_i[chi_{i-1}][2][chi_i] with bond
+    dimensions chi_i = min(chi, 2^(i+1), 2^(n-1-i)). No normalisation or
+    canonical form is imposed; each consumer brings them to canonical form
+    with its own code."""
+    rng = np.random.default_rng(seed)
+    dims = [1] + [min(chi, 2 ** (i + 1), 2 ** (n - 1 - i)) for i in range(n - 1)] + [1]
+    out = []
+    for i in range(n):
+        shape = (dims[i], 2, dims[i + 1])
+        a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        out.append(a.astype(dtype))
+    return out, dims
+
+
+# --------------------------------------------------------------------------
+# The five benchmark configurations of the workload (all synthetic).
+# N for TE-PAI follows the deep-Trotter baseline N(T) = N_dT (T/dT)^2 with
+# dT = 0.1 and N_dT = 20 (Sec. II.D, Eq. trotter-baseline-scaling).
+# --------------------------------------------------------------------------
+
+def trotter_baseline_steps(T: float, dT: float = 0.1, N_dT: int = 20) -> int:
+    return int(round(N_dT * (T / dT) ** 2))
+
+
+def config(idx: int) -> tuple[Problem, Params, dict]:
+    """Return (problem, params, extra) for configuration idx in 1..5."""
+    if idx == 1:
+        prob = spin_ring(8, 1.0, seed=0)
+        par = Params(T=1.0, n_steps=trotter_baseline_steps(1.0), delta=math.pi / 256,
+                     n_samples=1000, chi_max=16, cutoff=0.0, n_snapshots=10,
+                     seed=0, precision=0, obs_sites=np.array([0], dtype=np.int32))
+        return prob, par, {"trotter_steps": 100, "name": "ring8_heisenberg_T1"}
+    if idx == 2:
+        prob = spin_ring(32, 2.0, seed=0)
+        par = Params(T=2.0, n_steps=trotter_baseline_steps(2.0), delta=math.pi / 512,
+                     n_samples=10_000, chi_max=64, cutoff=1e-10, n_snapshots=20,
+                     seed=0, precision=1)
+        return prob, par, {"name": "ring32_heisenberg_T2"}
+    if idx == 3:
+        prob = spin_ring(64, 1.0, seed=0, Jz=0.5)
+        par = Params(T=3.0, n_steps=trotter_baseline_steps(3.0), delta=math.pi / 1024,
+                     n_samples=100_000, chi_max=128, cutoff=1e-10, n_snapshots=1,
+                     seed=0, precision=1)
+        return prob, par, {"name": "ring64_xxz_T3"}
+    if idx == 4:
+        prob = spin_ring(100, 3.0, seed=0)
+        par = Params(T=4.0, n_steps=trotter_baseline_steps(4.0), delta=math.pi / 1024,
+                     n_samples=50_000, chi_max=32, cutoff=1e-10, n_snapshots=1,
+                     seed=0, precision=1)
+        return prob, par, {"name": "ring100_heisenberg_T4", "chi_alt": 256}
+    if idx == 5:
+        prob = spin_ring(64, 1.0, seed=0)
+        par = Params(T=3.0, n_steps=trotter_baseline_steps(3.0), delta=math.pi / 1024,
+                     n_samples=20_000, chi_max=256, cutoff=1e-10, n_snapshots=1,
+                     seed=0, precision=1)
+        return prob, par, {"name": "ring64_hybrid_T2to5", "t0": 2.0}
+    raise ValueError(idx)
