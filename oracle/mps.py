@@ -14,6 +14,10 @@ in mixed-canonical form with an explicit orthogonality centre.
     k_cut   = the smallest k with sum_{j>=k} s_j^2 <= cutoff * sum_j s_j^2;
     k_floor = #{j : s_j > floor_rel * s_0}, which drops singular values that
               are zero to working precision.
+  A cut never splits a group of equal singular values: when
+  s_{k-1} - s_k <= gap_rel * s_0, k drops to the largest k' < k with a clear gap
+  there (the whole tied group is discarded), so that the truncated state is
+  unique. If no such k' >= 1 exists, k stays as it is.
 - A single-site gate, and a pi-rotation of a bond term (a product of two
   single-site Paulis), act on the physical index directly. A unitary on one
   site keeps every canonical condition.
@@ -97,7 +101,8 @@ def canonicalize(tensors) -> MPS:
     return m
 
 
-def keep_count(s: np.ndarray, chi_max: int, cutoff: float, floor_rel: float) -> int:
+def keep_count(s: np.ndarray, chi_max: int, cutoff: float, floor_rel: float,
+               gap_rel: float = 0.0) -> int:
     if s.size == 0 or s[0] <= 0.0:
         return 1
     w = s.astype(np.float64) ** 2
@@ -114,11 +119,18 @@ def keep_count(s: np.ndarray, chi_max: int, cutoff: float, floor_rel: float) -> 
             k_cut = k
             break
     k_floor = int(np.count_nonzero(s > floor_rel * s[0]))
-    return max(1, min(chi_max, k_floor, k_cut, s.size))
+    k = max(1, min(chi_max, k_floor, k_cut, s.size))
+    if k < s.size and s[k] > floor_rel * s[0]:
+        kk = k
+        while kk >= 1 and s[kk - 1] - s[kk] <= gap_rel * s[0]:
+            kk -= 1
+        if kk >= 1:
+            k = kk
+    return k
 
 
 def apply_two(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float,
-              floor_rel: float, swap: bool = False):
+              floor_rel: float, swap: bool = False, gap_rel: float = 1e-12):
     """Two-site update on bond (i, i+1) with a 4x4 gate g (basis |s_i s_{i+1}>)."""
     move_centre(m, i)
     A, B = m.A[i], m.A[i + 1]
@@ -127,7 +139,7 @@ def apply_two(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float,
     th = np.einsum('stuv,auvb->astb', g.reshape(2, 2, 2, 2), th)
     M = th.reshape(chl * 2, 2 * chr_)
     U, s, Vh = np.linalg.svd(M, full_matrices=False)
-    k = keep_count(s, chi_max, cutoff, floor_rel)
+    k = keep_count(s, chi_max, cutoff, floor_rel, gap_rel)
     tot = float(np.sum(s.astype(np.float64) ** 2))
     kept = s[:k]
     disc = 0.0 if tot == 0.0 else float(np.sum(s[k:] ** 2)) / tot
@@ -165,7 +177,7 @@ class GateCache:
 
 
 def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
-                cutoff: float, floor_rel: float):
+                cutoff: float, floor_rel: float, gap_rel: float = 1e-12):
     t = plan.terms[k]
     g = cache.get(k, v)
     if t.pauli == 'Z':
@@ -178,42 +190,49 @@ def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
         return
     n = m.n
     if t.b == t.a + 1:
-        apply_two(m, t.a, g, chi_max, cutoff, floor_rel)
+        apply_two(m, t.a, g, chi_max, cutoff, floor_rel, gap_rel=gap_rel)
         return
     # ring bond (n-1, 0): route site n-1 next to site 0 by swaps
     assert t.a == n - 1 and t.b == 0
     for p in range(n - 2, 0, -1):
-        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True)
+        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel)
     # chain bond (0, 1) now holds (site 0, site n-1): reorder the gate basis
     g01 = gates.SWAP @ g @ gates.SWAP
-    apply_two(m, 0, g01, chi_max, cutoff, floor_rel)
+    apply_two(m, 0, g01, chi_max, cutoff, floor_rel, gap_rel=gap_rel)
     for p in range(1, n - 1):
-        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True)
+        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel)
 
 
 def expect_z(m: MPS) -> np.ndarray:
-    """<Z_i> / <psi|psi> for all sites by left and right environments."""
+    """<Z_i> / <psi|psi> for all sites by left and right environments,
+    contracted pairwise:
+      L_{i+1}[c,d] = sum_{a,b,s} L_i[a,b] conj(A[a,s,c]) A[b,s,d]
+      R_i[a,b]     = sum_{c,d,s} conj(A[a,s,c]) A[b,s,d] R_{i+1}[c,d]
+      <Z_i>        = sum L_i[a,b] conj(A[a,s,c]) z_s A[b,s,d] R_{i+1}[c,d] / L_n."""
     n = m.n
     Lenv = [np.ones((1, 1), dtype=np.complex128)]
     for i in range(n):
         A = m.A[i]
-        Lenv.append(np.einsum('ab,asc,bsd->cd', Lenv[i], A.conj(), A))
+        T = np.tensordot(Lenv[i], A, axes=(1, 0))                    # [a,s,d]
+        Lenv.append(np.tensordot(A.conj(), T, axes=([0, 1], [0, 1])))  # [c,d]
     Renv = [None] * (n + 1)
     Renv[n] = np.ones((1, 1), dtype=np.complex128)
     for i in range(n - 1, -1, -1):
         A = m.A[i]
-        Renv[i] = np.einsum('asc,bsd,cd->ab', A.conj(), A, Renv[i + 1])
+        U = np.tensordot(A, Renv[i + 1], axes=(2, 1))                # [b,s,c]
+        Renv[i] = np.tensordot(A.conj(), U, axes=([1, 2], [1, 2]))   # [a,b]
     norm = Lenv[n][0, 0].real
     out = np.zeros(n)
     for i in range(n):
         A = m.A[i]
-        out[i] = np.einsum('ab,asc,s,bsd,cd->', Lenv[i], A.conj(), ZDIAG, A,
-                           Renv[i + 1]).real / norm
+        T = np.tensordot(Lenv[i], A, axes=(1, 0))                    # [a,s,d]
+        T2 = np.tensordot(T, Renv[i + 1], axes=(2, 1))              # [a,s,c]
+        out[i] = np.sum(A.conj() * ZDIAG[None, :, None] * T2).real / norm
     return out
 
 
 def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
-               floor_rel: float = 1e-14) -> np.ndarray:
+               floor_rel: float = 1e-14, gap_rel: float = 1e-12) -> np.ndarray:
     cache = GateCache(plan)
     out = []
     e = 0
@@ -221,7 +240,7 @@ def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
     for js in snap_steps:
         while e < ne and events[e, 0] <= js:
             apply_event(m, plan, cache, int(events[e, 1]), int(events[e, 2]),
-                        chi_max, cutoff, floor_rel)
+                        chi_max, cutoff, floor_rel, gap_rel)
             e += 1
         out.append(expect_z(m))
     return np.array(out)

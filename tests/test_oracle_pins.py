@@ -269,13 +269,20 @@ def test_estimate_matches_plain_mean_and_std():
 # ---------------------------------------------------------------- truncation / MPS
 def test_keep_count_brute_force():
     rng = np.random.default_rng(2)
-    for _ in range(200):
+    for _ in range(400):
         s = np.sort(rng.exponential(1.0, rng.integers(1, 12)) ** 3)[::-1]
+        if len(s) > 2 and rng.random() < 0.5:          # plant a tied group
+            i = int(rng.integers(1, len(s) - 1))
+            s[i + 1] = s[i]
         chi, cut = int(rng.integers(1, 10)), float(10.0 ** rng.uniform(-6, -0.5))
-        k = M.keep_count(s, chi, cut, 1e-14)
+        k = M.keep_count(s, chi, cut, 1e-14, gap_rel=1e-12)
         tot = np.sum(s ** 2)
         ok = [kk for kk in range(1, len(s) + 1) if np.sum(s[kk:] ** 2) <= cut * tot]
-        assert k == max(1, min(chi, ok[0], len(s)))
+        k0 = max(1, min(chi, ok[0], len(s)))
+        # cuts allowed: the end, or a place with a strict gap; take the largest <= k0
+        allowed = [kk for kk in range(1, k0 + 1) if kk == len(s) or s[kk - 1] > s[kk]]
+        assert k == (max(allowed) if allowed else k0)
+        assert k == len(s) or s[k - 1] > s[k] or not allowed
 
 
 def test_truncated_update_discards_weight_per_eckart_young():
