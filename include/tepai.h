@@ -1,0 +1,175 @@
+/*
+ * tepai.h — C-ABI of the GB300 (sm_103a) MPS TE-PAI library (libtepai.so).
+ *
+ * Method: Hasselgren & Koczor, "Quantum-inspired classical simulation through
+ * randomized time evolution" (arXiv 2604.13144).
+ *
+ * The library evolves an ensemble of independently sampled TE-PAI circuits.
+ *   - Sampling (Sec. II.B protocol; App. A.3, Eq. settings / Eq. gammas):
+ *     every rotation R_k(theta_kj) of the N-step product formula is replaced
+ *     by I, R_k(sign(theta) Delta) or R_k(pi).
+ *   - Evolution (Sec. II.A): each circuit is evolved as its own matrix product
+ *     state, with two-site SVD updates truncated to chi_max / cutoff.
+ *   - Measurement: <Z_i> at M snapshot steps.
+ *   - Estimate (Sec. II.B; App. B): the signed, ||g(t)||_1-weighted ensemble
+ *     mean.
+ *
+ * Conventions that hold for every call:
+ *   - Host pointers are caller-owned. They are read or written only during
+ *     the call and are never retained.
+ *   - Device pointers (the tepai_dev_* calls) are also caller-owned, and must
+ *     stay valid until the work queued on the given stream has completed.
+ *   - The library allocates device memory only inside a tepai_ctx, which owns
+ *     it until tepai_destroy.
+ *   - Every call returns 0 (TEPAI_OK) or a TEPAI_ERR_* code; tepai_strerror
+ *     names it. No C++ exception crosses this boundary.
+ *   - Results depend only on (problem, params, seed, global sample index), not
+ *     on the launch configuration.
+ */
+#ifndef TEPAI_H
+#define TEPAI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define TEPAI_OK                    0
+#define TEPAI_ERR_INVALID_ARG       1  /* n < 2, chi_max < 1, non-finite input, M does not divide steps ... */
+#define TEPAI_ERR_THETA_EXCEEDS_DELTA 2 /* some |theta_k| > Delta, against the assumption of App. A.3 */
+#define TEPAI_ERR_OUT_OF_MEMORY     3
+#define TEPAI_ERR_CUDA              4  /* a CUDA runtime call failed; the CUDA error text is kept per thread */
+#define TEPAI_ERR_NOT_CONVERGED     5  /* reserved: a Jacobi SVD that hits its sweep cap is counted in
+                                          tepai_stats.n_not_converged and its result is still used */
+#define TEPAI_ERR_WORKSPACE_TOO_SMALL 6
+#define TEPAI_ERR_NO_DEVICE         7
+
+/* ---- variants and precisions ----------------------------------------- */
+#define TEPAI_UNBIASED 0  /* TE-PAI with settings A, B, C (App. A.3) */
+#define TEPAI_NO_PI    1  /* biased TE-PAI without pi-rotations (Statement 3; App. A.4) */
+#define TEPAI_TROTTER  2  /* deterministic first-order product formula (Eq. Trotter-Suzuki) */
+
+#define TEPAI_FP64  0     /* all tensor arithmetic in FP64 */
+#define TEPAI_MIXED 1     /* FP32 tensors and SVD; FP64 norms, truncation weights and reduction */
+
+/* Spin chain / ring of Sec. III, Eq. (spinRing):
+ * H = sum_i h_i Z_i + sum_b (Jx_b X X + Jy_b Y Y + Jz_b Z Z) on bond b = (b, b+1 mod n).
+ * Term order within one Trotter step: Z_0..Z_{n-1}, then per bond XX, YY, ZZ. */
+typedef struct {
+    int n;                         /* number of spins, >= 2 */
+    int periodic;                  /* 1 = ring (bond n-1 joins sites n-1 and 0) */
+    const double *Jx, *Jy, *Jz;    /* host, length n (ring) or n-1 (chain) */
+    const double *h;               /* host, length n */
+    const unsigned char *init_bits;/* host, length n; initial |b_0 b_1 ...>, |0> has Z = +1 */
+} tepai_problem;
+
+typedef struct {
+    double T;                      /* total evolution time of the product formula */
+    long long n_steps;             /* N: theta_k = 2 c_k T / N (App. A.3) */
+    double delta;                  /* Delta of setting B (Eq. settings) */
+    long long n_samples;           /* N_s of this call */
+    long long sample_offset;       /* global index of the first sample (shards use disjoint ranges) */
+    long long run_steps;           /* steps actually evolved, 0 = all N */
+    int chi_max;                   /* bond-dimension cap of every two-site update (Sec. II.A) */
+    double cutoff;                 /* keep the fewest singular values whose discarded weight
+                                      sum_{j>=k} s_j^2 <= cutoff * sum_j s_j^2 (then cap at chi_max) */
+    int n_snapshots;               /* M; snapshot m after step m * run_steps / M, must divide */
+    const int *obs_sites;          /* host, Z_i sites measured; NULL = all n */
+    int n_obs;
+    unsigned long long seed;       /* Philox4x64-10 key word 0 (key word 1 = global sample index) */
+    int variant;                   /* TEPAI_UNBIASED | TEPAI_NO_PI | TEPAI_TROTTER */
+    int precision;                 /* TEPAI_FP64 | TEPAI_MIXED */
+} tepai_params;
+
+/* Optional initial MPS shared by all samples (a "hybrid" start). Site tensors
+ * A_i[d_i][2][d_{i+1}] are row-major, complex interleaved (re, im), and
+ * concatenated over sites. They need not be normalised or canonical: every
+ * sample first brings them to right-canonical form. */
+typedef struct {
+    const int *bond_dims;          /* length n+1, bond_dims[0] = bond_dims[n] = 1, each <= chi_max */
+    const double *tensors;         /* host (tepai_run) or device (tepai_dev_*) */
+} tepai_mps;
+
+typedef struct {
+    double events;                 /* non-identity gates applied (nu, summed over samples) */
+    double gate_updates;           /* two-site SVD updates that apply a gate */
+    double swap_updates;           /* two-site SVD updates of ring-bond routing */
+    double qr_moves;               /* orthogonality-centre moves */
+    double jacobi_sweeps;          /* summed over all SVDs */
+    double max_discarded_weight;
+    double alg_flops;              /* 736 chi_l chi chi_r-style algorithmic count, see DESIGN */
+    int max_chi;
+    int n_not_converged;
+} tepai_stats;
+
+/* Circuit event of one sample: Trotter step j (1-based), term k, setting v
+ * (1 = B, 2 = C, 3 = deterministic Trotter gate). */
+typedef struct { int32_t j; int32_t k; int32_t v; int32_t pad; } tepai_event;
+
+typedef struct tepai_ctx tepai_ctx;
+
+/* ---- context ---------------------------------------------------------- */
+/* Create a context on CUDA device `cuda_device`, issuing work on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream). */
+int  tepai_create(tepai_ctx **out, int cuda_device, void *cuda_stream);
+void tepai_destroy(tepai_ctx *ctx);
+
+/* ---- host-buffer entry points (all buffers host memory) ---------------- */
+/* Full run (Sec. II.B protocol steps 1-3). Outputs, each [M][n_obs] row-major:
+ *   mean     ||g(t_m)||_1 * (1/N_s) sum_s sign_s,m v_s,m,i;
+ *   stderr_  ||g(t_m)||_1 * sqrt(Var[v]/N_s) (Statement 2), may be NULL;
+ *   partials [M][n_obs][3] = (Neumaier sum, compensation, sum of squares)
+ *            of sign*v over this call's samples, so that shards can be merged;
+ *            may be NULL.
+ * `init` may be NULL (product state init_bits). stats may be NULL. */
+int tepai_run(tepai_ctx *ctx, const tepai_problem *prob, const tepai_params *par,
+              const tepai_mps *init, double *mean, double *stderr_, double *partials,
+              tepai_stats *stats);
+
+/* Per-sample values for parity checks: v [n_samples][M][n_obs] = <Z_i>/<psi|psi>
+ * after step j_m, and sign [n_samples][M] = (-1)^{#C up to j_m} (App. B). */
+int tepai_sample_values(tepai_ctx *ctx, const tepai_problem *prob, const tepai_params *par,
+                        const tepai_mps *init, double *v, signed char *sign, tepai_stats *stats);
+
+/* The events of global sample `sample`, drawn by the device sampler, in gate
+ * order. Writes min(count, cap) events to buf and the full count to *count. */
+int tepai_export_circuit(tepai_ctx *ctx, const tepai_problem *prob, const tepai_params *par,
+                         long long sample, tepai_event *buf, long long cap, long long *count);
+
+/* Host planner only: g[m] = ||g(t_m)||_1 (App. A.6, finite-N product) and the
+ * expected gate count per sample E[nu] = run_steps * sum_k q_k. */
+int tepai_gnorm(const tepai_problem *prob, const tepai_params *par, double *g, double *expected_nu);
+
+/* ---- device-resident entry points -------------------------------------- */
+/* Bytes of device workspace for a call with at most `grid_ctas` CTAs
+ * (0 = library default for this device). */
+int tepai_dev_workspace_size(const tepai_problem *prob, const tepai_params *par,
+                             int grid_ctas, size_t *bytes);
+/* Plan on the host and upload the tables and the initial MPS (device
+ * pointers in `init`, or NULL) into the caller's workspace, on `stream`. */
+int tepai_dev_prepare(const tepai_problem *prob, const tepai_params *par, const tepai_mps *init,
+                      void *d_workspace, size_t ws_bytes, int grid_ctas, void *stream);
+/* Launch the ensemble on a prepared workspace: kernels only, no host
+ * synchronisation, no allocation. Device outputs: d_mean/d_stderr [M][n_obs],
+ * d_partials [M][n_obs][3], d_v [n_samples][M][n_obs], d_sign [n_samples][M]
+ * (any may be NULL except d_mean). */
+int tepai_dev_execute(void *d_workspace, double *d_mean, double *d_stderr, double *d_partials,
+                      double *d_v, signed char *d_sign, void *stream);
+/* Point a prepared workspace at another range of global sample indices
+ * [offset, offset + n_samples): the next execute evolves those circuits. Host
+ * bookkeeping only (no device work); the Philox key word 1 of sample s is s. */
+int tepai_dev_set_sample_offset(void *d_workspace, long long sample_offset);
+/* Copy the device statistics of the last execute on this workspace. Synchronises `stream`. */
+int tepai_dev_stats(void *d_workspace, tepai_stats *stats, void *stream);
+
+const char *tepai_strerror(int code);
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *tepai_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TEPAI_H */

@@ -1,0 +1,434 @@
+// C-ABI of libtepai.so: workspace layout, launches and host-buffer wrappers.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "host_plan.h"
+
+namespace tepai {
+cudaError_t launch_ensemble_f32(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_ensemble_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t occupancy_ensemble_f32(int block, size_t smem, int* ctas_per_sm);
+cudaError_t occupancy_ensemble_f64(int block, size_t smem, int* ctas_per_sm);
+cudaError_t launch_signed_reduce(const double* v, const signed char* sign, long long ns, int M, int nobs,
+                                 const double* gnorm, double* mean, double* se, double* part, cudaStream_t st);
+cudaError_t launch_export_circuit(const KArgs& a, unsigned long long s, int* buf, long long cap,
+                                  unsigned long long* count, cudaStream_t st);
+}  // namespace tepai
+
+using namespace tepai;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+int cuda_fail(cudaError_t e) {
+  g_cuda_err = cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? TEPAI_ERR_OUT_OF_MEMORY : TEPAI_ERR_CUDA;
+}
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return cuda_fail(e_); } while (0)
+
+inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Jacobi tolerance, singular-value floor and sweep cap per precision.
+// Singular values closer than gap_rel * s_0 count as one degenerate group at a cut.
+struct NumCfg { double tol, floor_rel, gap_rel; int max_sweeps; int csize; };
+NumCfg num_cfg(int precision) {
+  if (precision == TEPAI_FP64) return {16 * 1.1102230246251565e-16, 1e-14, 1e-12, 60, 16};
+  return {16 * 5.9604644775390625e-08, 4e-6, 1e-5, 40, 8};
+}
+
+struct Layout {
+  size_t terms, snaps, gnorm, obs, bits, dims, init, stats, counter, v, sign, arena, stride, total;
+};
+
+Layout layout(const HostPlan& hp, const tepai_params* Q, int grid, bool has_init, size_t init_elems) {
+  const NumCfg nc = num_cfg(Q->precision);
+  const size_t cap = (size_t)Q->chi_max;
+  Layout L{};
+  size_t o = 0;
+  L.terms = o; o = al256(o + sizeof(TermDev) * hp.L);
+  L.snaps = o; o = al256(o + sizeof(int) * hp.M);
+  L.gnorm = o; o = al256(o + sizeof(double) * hp.M);
+  L.obs = o; o = al256(o + sizeof(int) * hp.n_obs);
+  L.bits = o; o = al256(o + hp.n);
+  L.dims = o; o = al256(o + sizeof(int) * (hp.n + 1));
+  L.init = o; o = al256(o + (has_init ? sizeof(double) * 2 * init_elems : 0));
+  L.stats = o; o = al256(o + sizeof(DevStats));
+  L.counter = o; o = al256(o + sizeof(unsigned long long));
+  L.v = o; o = al256(o + sizeof(double) * (size_t)Q->n_samples * hp.M * hp.n_obs);
+  L.sign = o; o = al256(o + (size_t)Q->n_samples * hp.M);
+  L.stride = al256(((size_t)hp.n * 2 * cap * cap + 8 * cap * cap) * nc.csize);
+  L.arena = o; o = al256(o + L.stride * (size_t)grid);
+  L.total = o;
+  return L;
+}
+
+struct Prepared {
+  KArgs ka;
+  int precision, grid, block;
+  size_t smem;
+  long long n_samples;
+  int M, n_obs;
+  double* gnorm;
+  DevStats* stats;
+  cudaStream_t stream;
+};
+
+std::mutex g_mu;
+std::unordered_map<void*, Prepared> g_reg;
+
+struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems; };
+
+int launch_shape(const HostPlan& hp, const tepai_params* Q, int grid_req, LaunchShape& ls) {
+  const NumCfg nc = num_cfg(Q->precision);
+  const int cap = Q->chi_max;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  int sms = 0, optin = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  ls.block = cap >= 64 ? 512 : 256;
+  const size_t fixed = smem_fixed_bytes(hp.n, hp.L, cap, nc.csize);
+  const size_t xbytes = (size_t)4 * cap * cap * nc.csize;
+  if (fixed + xbytes <= (size_t)optin) {
+    ls.smem = fixed + xbytes; ls.x_in_smem = 1; ls.x_elems = 4 * cap * cap;
+  } else {
+    ls.smem = fixed; ls.x_in_smem = 0; ls.x_elems = 0;
+  }
+  if (grid_req > 0) {
+    ls.grid = grid_req;
+  } else {
+    int per_sm = 1;
+    CK(Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(ls.block, ls.smem, &per_sm)
+                                  : occupancy_ensemble_f32(ls.block, ls.smem, &per_sm));
+    if (per_sm < 1) per_sm = 1;
+    ls.grid = sms * per_sm;
+  }
+  if (Q->n_samples > 0 && ls.grid > Q->n_samples) ls.grid = (int)Q->n_samples;
+  if (ls.grid < 1) ls.grid = 1;
+  return TEPAI_OK;
+}
+
+int check_init(const HostPlan& hp, const tepai_params* Q, const tepai_mps* init, size_t& elems) {
+  elems = 0;
+  if (!init) return TEPAI_OK;
+  if (!init->bond_dims || !init->tensors) return TEPAI_ERR_INVALID_ARG;
+  const int* d = init->bond_dims;
+  if (d[0] != 1 || d[hp.n] != 1) return TEPAI_ERR_INVALID_ARG;
+  for (int i = 0; i <= hp.n; ++i)
+    if (d[i] < 1 || d[i] > Q->chi_max) return TEPAI_ERR_INVALID_ARG;
+  for (int i = 0; i < hp.n; ++i) elems += (size_t)d[i] * 2 * d[i + 1];
+  return TEPAI_OK;
+}
+
+int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps* init, bool init_on_host,
+                 void* ws, size_t ws_bytes, int grid_req, cudaStream_t st) {
+  HostPlan hp;
+  int rc = build_plan(P, Q, hp);
+  if (rc) return rc;
+  if (Q->n_samples < 1 || !ws) return TEPAI_ERR_INVALID_ARG;
+  size_t init_elems = 0;
+  rc = check_init(hp, Q, init, init_elems);
+  if (rc) return rc;
+  LaunchShape ls;
+  rc = launch_shape(hp, Q, grid_req, ls);
+  if (rc) return rc;
+  const Layout L = layout(hp, Q, ls.grid, init != nullptr, init_elems);
+  if (L.total > ws_bytes) return TEPAI_ERR_WORKSPACE_TOO_SMALL;
+  char* base = static_cast<char*>(ws);
+  CK(cudaMemcpyAsync(base + L.terms, hp.terms.data(), sizeof(TermDev) * hp.L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + L.snaps, hp.snaps.data(), sizeof(int) * hp.M, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + L.gnorm, hp.gnorm.data(), sizeof(double) * hp.M, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + L.obs, hp.obs.data(), sizeof(int) * hp.n_obs, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + L.bits, hp.bits.data(), hp.n, cudaMemcpyHostToDevice, st));
+  if (init) {
+    CK(cudaMemcpyAsync(base + L.dims, init->bond_dims, sizeof(int) * (hp.n + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(base + L.init, init->tensors, sizeof(double) * 2 * init_elems,
+                       init_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  }
+  // the host vectors die with this call: wait for the copies to finish
+  CK(cudaStreamSynchronize(st));
+  const NumCfg nc = num_cfg(Q->precision);
+  Prepared pr{};
+  KArgs& a = pr.ka;
+  a.n = hp.n; a.L = hp.L; a.M = hp.M; a.n_obs = hp.n_obs; a.chi_cap = Q->chi_max;
+  a.periodic = hp.periodic; a.variant = Q->variant; a.max_sweeps = nc.max_sweeps;
+  a.N = hp.N; a.run_steps = hp.run_steps; a.n_samples = Q->n_samples; a.sample_offset = Q->sample_offset;
+  a.seed = Q->seed; a.cutoff = Q->cutoff; a.floor_rel = nc.floor_rel; a.tol = nc.tol; a.gap_rel = nc.gap_rel;
+  a.terms = reinterpret_cast<const TermDev*>(base + L.terms);
+  a.snaps = reinterpret_cast<const int*>(base + L.snaps);
+  a.obs = reinterpret_cast<const int*>(base + L.obs);
+  a.init_bits = reinterpret_cast<const unsigned char*>(base + L.bits);
+  a.init_dims = init ? reinterpret_cast<const int*>(base + L.dims) : nullptr;
+  a.init_tensors = init ? reinterpret_cast<const double*>(base + L.init) : nullptr;
+  a.arena = base + L.arena; a.arena_stride = L.stride;
+  a.v = reinterpret_cast<double*>(base + L.v);
+  a.sign = reinterpret_cast<signed char*>(base + L.sign);
+  a.stats = reinterpret_cast<DevStats*>(base + L.stats);
+  a.counter = reinterpret_cast<unsigned long long*>(base + L.counter);
+  a.x_in_smem = ls.x_in_smem; a.smem_x_elems = ls.x_elems;
+  pr.precision = Q->precision; pr.grid = ls.grid; pr.block = ls.block; pr.smem = ls.smem;
+  pr.n_samples = Q->n_samples; pr.M = hp.M; pr.n_obs = hp.n_obs;
+  pr.gnorm = reinterpret_cast<double*>(base + L.gnorm);
+  pr.stats = a.stats;
+  pr.stream = st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_reg[ws] = pr;
+  return TEPAI_OK;
+}
+
+int execute_impl(void* ws, double* d_mean, double* d_se, double* d_part, double* d_v, signed char* d_sign,
+                 cudaStream_t st) {
+  Prepared pr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_reg.find(ws);
+    if (it == g_reg.end()) return TEPAI_ERR_INVALID_ARG;
+    pr = it->second;
+  }
+  const KArgs& a = pr.ka;
+  CK(cudaMemsetAsync(a.stats, 0, sizeof(DevStats), st));
+  CK(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st));
+  CK(pr.precision == TEPAI_FP64 ? launch_ensemble_f64(a, pr.grid, pr.block, pr.smem, st)
+                                : launch_ensemble_f32(a, pr.grid, pr.block, pr.smem, st));
+  if (d_mean || d_se || d_part)
+    CK(launch_signed_reduce(a.v, a.sign, pr.n_samples, pr.M, pr.n_obs, pr.gnorm, d_mean, d_se, d_part, st));
+  const size_t nv = (size_t)pr.n_samples * pr.M * pr.n_obs;
+  if (d_v) CK(cudaMemcpyAsync(d_v, a.v, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+  if (d_sign) CK(cudaMemcpyAsync(d_sign, a.sign, (size_t)pr.n_samples * pr.M, cudaMemcpyDeviceToDevice, st));
+  return TEPAI_OK;
+}
+
+int stats_impl(void* ws, tepai_stats* out, cudaStream_t st) {
+  Prepared pr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_reg.find(ws);
+    if (it == g_reg.end()) return TEPAI_ERR_INVALID_ARG;
+    pr = it->second;
+  }
+  DevStats ds;
+  CK(cudaMemcpyAsync(&ds, pr.stats, sizeof(ds), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  out->events = (double)ds.events;
+  out->gate_updates = (double)ds.gate_updates;
+  out->swap_updates = (double)ds.swap_updates;
+  out->qr_moves = (double)ds.qr_moves;
+  out->jacobi_sweeps = (double)ds.sweeps;
+  out->max_discarded_weight = ds.max_discarded;
+  out->alg_flops = ds.alg_flops;
+  out->max_chi = ds.max_chi;
+  out->n_not_converged = (int)ds.not_converged;
+  return TEPAI_OK;
+}
+
+}  // namespace
+
+struct tepai_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* out = nullptr;
+  size_t out_bytes = 0;
+};
+
+namespace {
+int ctx_reserve(tepai_ctx* c, size_t ws_bytes, size_t out_bytes) {
+  if (ws_bytes > c->ws_bytes) {
+    if (c->ws) {
+      std::lock_guard<std::mutex> lk(g_mu);
+      g_reg.erase(c->ws);
+    }
+    if (c->ws) CK(cudaFree(c->ws));
+    c->ws = nullptr; c->ws_bytes = 0;
+    CK(cudaMalloc(&c->ws, ws_bytes));
+    c->ws_bytes = ws_bytes;
+  }
+  if (out_bytes > c->out_bytes) {
+    if (c->out) CK(cudaFree(c->out));
+    c->out = nullptr; c->out_bytes = 0;
+    CK(cudaMalloc(&c->out, out_bytes));
+    c->out_bytes = out_bytes;
+  }
+  return TEPAI_OK;
+}
+
+int ctx_run(tepai_ctx* c, const tepai_problem* P, const tepai_params* Q, const tepai_mps* init,
+            double* mean, double* se, double* part, double* v, signed char* sign, tepai_stats* stats) {
+  if (!c) return TEPAI_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  size_t bytes = 0;
+  int rc = tepai_dev_workspace_size(P, Q, 0, &bytes);
+  if (rc) return rc;
+  HostPlan hp;
+  rc = build_plan(P, Q, hp);
+  if (rc) return rc;
+  const size_t mo = (size_t)hp.M * hp.n_obs;
+  const size_t nv = (size_t)Q->n_samples * mo;
+  const size_t out_bytes = sizeof(double) * (5 * mo + (v ? nv : 0)) + (sign ? (size_t)Q->n_samples * hp.M : 0) + 256;
+  rc = ctx_reserve(c, bytes, out_bytes);
+  if (rc) return rc;
+  rc = prepare_impl(P, Q, init, true, c->ws, c->ws_bytes, 0, c->stream);
+  if (rc) return rc;
+  double* d_mean = c->out;
+  double* d_se = d_mean + mo;
+  double* d_part = d_se + mo;
+  double* d_v = d_part + 3 * mo;
+  signed char* d_sign = reinterpret_cast<signed char*>(d_v + (v ? nv : 0));
+  rc = execute_impl(c->ws, d_mean, d_se, d_part, v ? d_v : nullptr, sign ? d_sign : nullptr, c->stream);
+  if (rc) return rc;
+  if (mean) CK(cudaMemcpyAsync(mean, d_mean, sizeof(double) * mo, cudaMemcpyDeviceToHost, c->stream));
+  if (se) CK(cudaMemcpyAsync(se, d_se, sizeof(double) * mo, cudaMemcpyDeviceToHost, c->stream));
+  if (part) CK(cudaMemcpyAsync(part, d_part, sizeof(double) * 3 * mo, cudaMemcpyDeviceToHost, c->stream));
+  if (v) CK(cudaMemcpyAsync(v, d_v, sizeof(double) * nv, cudaMemcpyDeviceToHost, c->stream));
+  if (sign) CK(cudaMemcpyAsync(sign, d_sign, (size_t)Q->n_samples * hp.M, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  if (stats) { rc = stats_impl(c->ws, stats, c->stream); if (rc) return rc; }
+  return TEPAI_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int tepai_create(tepai_ctx** out, int cuda_device, void* cuda_stream) {
+  if (!out) return TEPAI_ERR_INVALID_ARG;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) { g_cuda_err = e != cudaSuccess ? cudaGetErrorString(e) : "no device"; return TEPAI_ERR_NO_DEVICE; }
+  if (cuda_device < 0 || cuda_device >= ndev) return TEPAI_ERR_INVALID_ARG;
+  tepai_ctx* c = new tepai_ctx();
+  c->device = cuda_device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = c;
+  return TEPAI_OK;
+}
+
+void tepai_destroy(tepai_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->ws) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_reg.erase(c->ws);
+  }
+  if (c->ws) cudaFree(c->ws);
+  if (c->out) cudaFree(c->out);
+  delete c;
+}
+
+int tepai_run(tepai_ctx* c, const tepai_problem* P, const tepai_params* Q, const tepai_mps* init,
+              double* mean, double* stderr_, double* partials, tepai_stats* stats) {
+  if (!mean) return TEPAI_ERR_INVALID_ARG;
+  return ctx_run(c, P, Q, init, mean, stderr_, partials, nullptr, nullptr, stats);
+}
+
+int tepai_sample_values(tepai_ctx* c, const tepai_problem* P, const tepai_params* Q, const tepai_mps* init,
+                        double* v, signed char* sign, tepai_stats* stats) {
+  if (!v || !sign) return TEPAI_ERR_INVALID_ARG;
+  return ctx_run(c, P, Q, init, nullptr, nullptr, nullptr, v, sign, stats);
+}
+
+int tepai_export_circuit(tepai_ctx* c, const tepai_problem* P, const tepai_params* Q, long long sample,
+                         tepai_event* buf, long long cap, long long* count) {
+  if (!c || !count || (cap > 0 && !buf) || sample < 0) return TEPAI_ERR_INVALID_ARG;
+  HostPlan hp;
+  int rc = build_plan(P, Q, hp);
+  if (rc) return rc;
+  CK(cudaSetDevice(c->device));
+  const size_t tb = al256(sizeof(TermDev) * hp.L);
+  const size_t need = tb + 256 + sizeof(tepai_event) * (size_t)(cap > 0 ? cap : 1);
+  rc = ctx_reserve(c, need, 0);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_reg.erase(c->ws);
+  }
+  char* base = static_cast<char*>(c->ws);
+  CK(cudaMemcpyAsync(base, hp.terms.data(), sizeof(TermDev) * hp.L, cudaMemcpyHostToDevice, c->stream));
+  KArgs a{};
+  a.n = hp.n; a.L = hp.L; a.variant = Q->variant; a.run_steps = hp.run_steps; a.seed = Q->seed;
+  a.terms = reinterpret_cast<const TermDev*>(base);
+  unsigned long long* d_count = reinterpret_cast<unsigned long long*>(base + tb);
+  int* d_buf = reinterpret_cast<int*>(base + tb + 256);
+  CK(launch_export_circuit(a, (unsigned long long)sample, d_buf, cap, d_count, c->stream));
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const long long ncopy = (long long)cnt < cap ? (long long)cnt : cap;
+  if (ncopy > 0)
+    CK(cudaMemcpy(buf, d_buf, sizeof(tepai_event) * (size_t)ncopy, cudaMemcpyDeviceToHost));
+  *count = (long long)cnt;
+  return TEPAI_OK;
+}
+
+int tepai_gnorm(const tepai_problem* P, const tepai_params* Q, double* g, double* expected_nu) {
+  HostPlan hp;
+  const int rc = build_plan(P, Q, hp);
+  if (rc) return rc;
+  if (g) for (int m = 0; m < hp.M; ++m) g[m] = hp.gnorm[m];
+  if (expected_nu) *expected_nu = hp.expected_nu;
+  return TEPAI_OK;
+}
+
+int tepai_dev_workspace_size(const tepai_problem* P, const tepai_params* Q, int grid_ctas, size_t* bytes) {
+  if (!bytes) return TEPAI_ERR_INVALID_ARG;
+  HostPlan hp;
+  int rc = build_plan(P, Q, hp);
+  if (rc) return rc;
+  if (Q->n_samples < 1) return TEPAI_ERR_INVALID_ARG;
+  LaunchShape ls;
+  rc = launch_shape(hp, Q, grid_ctas, ls);
+  if (rc) return rc;
+  size_t init_elems = 0;
+  // room for an initial MPS at the bond-dimension cap on every bond
+  init_elems = (size_t)hp.n * 2 * Q->chi_max * Q->chi_max;
+  *bytes = layout(hp, Q, ls.grid, true, init_elems).total;
+  return TEPAI_OK;
+}
+
+int tepai_dev_prepare(const tepai_problem* P, const tepai_params* Q, const tepai_mps* init, void* d_ws,
+                      size_t ws_bytes, int grid_ctas, void* stream) {
+  return prepare_impl(P, Q, init, false, d_ws, ws_bytes, grid_ctas, static_cast<cudaStream_t>(stream));
+}
+
+int tepai_dev_execute(void* d_ws, double* d_mean, double* d_stderr, double* d_partials, double* d_v,
+                      signed char* d_sign, void* stream) {
+  if (!d_ws || !d_mean) return TEPAI_ERR_INVALID_ARG;
+  return execute_impl(d_ws, d_mean, d_stderr, d_partials, d_v, d_sign, static_cast<cudaStream_t>(stream));
+}
+
+int tepai_dev_set_sample_offset(void* d_ws, long long sample_offset) {
+  if (!d_ws || sample_offset < 0) return TEPAI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_reg.find(d_ws);
+  if (it == g_reg.end()) return TEPAI_ERR_INVALID_ARG;
+  it->second.ka.sample_offset = sample_offset;
+  return TEPAI_OK;
+}
+
+int tepai_dev_stats(void* d_ws, tepai_stats* stats, void* stream) {
+  if (!d_ws || !stats) return TEPAI_ERR_INVALID_ARG;
+  return stats_impl(d_ws, stats, static_cast<cudaStream_t>(stream));
+}
+
+const char* tepai_strerror(int code) {
+  switch (code) {
+    case TEPAI_OK: return "ok";
+    case TEPAI_ERR_INVALID_ARG: return "invalid argument";
+    case TEPAI_ERR_THETA_EXCEEDS_DELTA: return "|theta_k| > Delta: the PAI decomposition needs |theta| <= Delta <= pi";
+    case TEPAI_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case TEPAI_ERR_CUDA: return "CUDA runtime error";
+    case TEPAI_ERR_NOT_CONVERGED: return "Jacobi SVD reached its sweep cap";
+    case TEPAI_ERR_WORKSPACE_TOO_SMALL: return "device workspace too small";
+    case TEPAI_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown error";
+  }
+}
+
+const char* tepai_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Shared device/host definitions of the MPS TE-PAI CUDA path.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tepai {
+
+// ---------------------------------------------------------------- complex
+template <typename R> struct cplx { R re, im; };
+
+template <typename R> __host__ __device__ __forceinline__ cplx<R> mk(R a, R b) { return {a, b}; }
+template <typename R> __host__ __device__ __forceinline__ cplx<R> add(cplx<R> a, cplx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> __host__ __device__ __forceinline__ cplx<R> sub(cplx<R> a, cplx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> __host__ __device__ __forceinline__ cplx<R> mul(cplx<R> a, cplx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <typename R> __host__ __device__ __forceinline__ cplx<R> cmul(cplx<R> a, cplx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <typename R> __host__ __device__ __forceinline__ cplx<R> scale(cplx<R> a, R s) { return {a.re * s, a.im * s}; }
+template <typename R> __host__ __device__ __forceinline__ R abs2(cplx<R> a) { return a.re * a.re + a.im * a.im; }
+// acc += a * b
+template <typename R> __host__ __device__ __forceinline__ void fma_c(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re); acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im); acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename R> __host__ __device__ __forceinline__ void fma_cc(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re); acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im); acc.im = fma(-a.im, b.re, acc.im);
+}
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon et al., SC'11: ten rounds of two 64x64->128-bit products with Weyl
+// key increments. Key = (seed, global sample index); counter = (j, k, 0, 0).
+struct u64x4 { unsigned long long x0, x1, x2, x3; };
+
+__device__ __forceinline__ u64x4 philox4x64_10(u64x4 c, unsigned long long k0, unsigned long long k1) {
+  const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    unsigned long long hi0 = __umul64hi(M0, c.x0), lo0 = M0 * c.x0;
+    unsigned long long hi1 = __umul64hi(M1, c.x2), lo1 = M1 * c.x2;
+    c = u64x4{hi1 ^ c.x1 ^ k0, lo1, hi0 ^ c.x3 ^ k1, lo0};
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------- tables
+// One Hamiltonian term k, built by the host planner (FP64).
+struct TermDev {
+  int kind;       // 0 = single-site Z_a, 1 = bond term P_a P_b
+  int a, b;       // sites acted on (b == a for kind 0)
+  int pauli;      // 0 = X, 1 = Y, 2 = Z
+  int pad;
+  unsigned long long thr_event;  // gate (j,k) is not A when x0 < thr_event
+  unsigned long long thr_c;      // ... and is C when x1 < thr_c
+  double g[32];   // gate of setting B (or the Trotter gate): 4x4 complex row-major,
+                  // basis |s_a s_b>, (re,im) interleaved; kind 0 uses g[0..7] as 2x2.
+};
+
+struct DevStats {
+  unsigned long long events, gate_updates, swap_updates, qr_moves, sweeps, not_converged;
+  int max_chi, pad;
+  double max_discarded;
+  double alg_flops;
+};
+
+struct KArgs {
+  int n, L, M, n_obs, chi_cap, periodic, variant, max_sweeps;
+  long long N, run_steps, n_samples, sample_offset;
+  unsigned long long seed;
+  double cutoff, floor_rel, tol, gap_rel;
+  const TermDev* terms;
+  const int* snaps;          // [M] snapshot steps
+  const int* obs;            // [n_obs]
+  const int* init_dims;      // [n+1] or nullptr
+  const double* init_tensors;// complex interleaved FP64, or nullptr
+  const unsigned char* init_bits;  // [n]
+  char* arena;               // per-CTA arena base
+  size_t arena_stride;       // bytes per CTA
+  double* v;                 // [n_samples][M][n_obs]
+  signed char* sign;         // [n_samples][M]
+  DevStats* stats;
+  unsigned long long* counter;  // work-queue head
+  int x_in_smem;             // the SVD working matrix lives in shared memory
+  int smem_x_elems;          // capacity of that buffer (complex elements)
+};
+
+// Device-visible status word of the ensemble launch.
+enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BAD_DIM = 2 };
+
+__host__ __device__ inline size_t align_up(size_t x, size_t al) { return (x + al - 1) / al * al; }
+
+// Fixed shared-memory bytes of the engine for (n, L, cap, sizeof complex).
+__host__ __device__ inline size_t smem_fixed_bytes(int n, int L, int cap, int csize) {
+  size_t b = 0;
+  b += align_up((size_t)(n + 1) * 4, 16);          // dims
+  b += align_up((size_t)L, 16);                     // flags
+  b += 64 * 8;                                      // red
+  b += align_up((size_t)2 * cap * 8, 16);           // wn
+  b += align_up((size_t)2 * cap * 4, 16);           // perm
+  b += align_up((size_t)n * 8, 16);                 // zval
+  b += 16 * 4 + 16 * 8;                             // ibuf, dbuf
+  b += align_up((size_t)3 * 2 * cap * csize, 16);   // Householder scalars
+  return align_up(b, 128);
+}
+
+}  // namespace tepai

@@ -1,0 +1,114 @@
+// Per-sample MPS engine: one CTA evolves one TE-PAI circuit at a time.
+//
+// State of the CTA, in global memory (the CTA's arena slot, mostly L2-resident):
+//   sites  n slots of 2*cap*cap complex, A_i[d_i][2][d_{i+1}] dense row-major
+//   TH     4*cap*cap complex: theta' row-major, also QR panel / environments
+//   XG     4*cap*cap complex: SVD working matrix when it does not fit in shared
+//          memory, also the Q factor and temporaries
+// State in shared memory: bond dims, step flags, sort keys, reductions, and
+// the SVD working matrix X when it fits.
+// Every member function is called by all threads of the CTA with uniform
+// arguments; they synchronise internally.
+#pragma once
+#include "common.cuh"
+
+namespace tepai {
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread gets the result. `red` holds >= 33 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double r = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    r = warp_sum(r);
+    if (threadIdx.x == 0) red[32] = r;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+template <typename R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
+
+// SVD tolerances and floors of one precision.
+template <typename R> struct Prec;
+template <> struct Prec<float>  { static constexpr double eps = 5.9604644775390625e-08; };
+template <> struct Prec<double> { static constexpr double eps = 1.1102230246251565e-16; };
+
+struct LocalStats {
+  unsigned long long events = 0, gate_updates = 0, swap_updates = 0, qr_moves = 0, sweeps = 0,
+                     not_converged = 0;
+  int max_chi = 1;
+  double max_discarded = 0.0, alg_flops = 0.0;
+};
+
+// Shared-memory scratch of the engine (fixed part); X follows when it fits.
+struct SmemLayout {
+  int* dims;          // [n+1]
+  unsigned char* flags;  // [L]
+  double* red;        // [64]
+  double* wn;         // [2*cap] squared column norms
+  int* perm;          // [2*cap]
+  double* zval;       // [n]
+  int* ibuf;          // [16]
+  double* dbuf;       // [16]
+  void* hh;           // Householder scalars: 3 arrays of [2*cap] complex<double>-sized slots
+  void* x;            // SVD working matrix (optional)
+};
+
+template <typename R>
+struct Engine {
+  using C = cplx<R>;
+  const KArgs& a;
+  SmemLayout sm;
+  C* site0;
+  size_t slot;        // complex elements per site slot
+  C* TH;
+  C* XG;
+  int cap;            // bond-dimension cap (chi_max)
+  int centre;
+  LocalStats st;
+
+  __device__ Engine(const KArgs& args, SmemLayout s, char* arena)
+      : a(args), sm(s), cap(args.chi_cap), centre(0) {
+    slot = (size_t)2 * cap * cap;
+    site0 = reinterpret_cast<C*>(arena);
+    TH = site0 + (size_t)a.n * slot;
+    XG = TH + (size_t)4 * cap * cap;
+  }
+
+  __device__ __forceinline__ C* S(int i) const { return site0 + (size_t)i * slot; }
+  __device__ __forceinline__ int tid() const { return threadIdx.x; }
+  __device__ __forceinline__ int nt() const { return blockDim.x; }
+
+  // state preparation
+  __device__ void init_product();
+  __device__ void init_from_tensors();
+  // single-site unitary u (2x2 row-major) on site i
+  __device__ void apply_1site(int i, const C u[4]);
+  // centre moves
+  __device__ void move_centre(int target);
+  __device__ void qr_right();
+  __device__ void qr_left();
+  __device__ void householder(C* Y, int m, int nq, C* Q);
+  // two-site update on bond (i, i+1) with gate g (basis |s_i s_{i+1}>)
+  __device__ void two_site(int i, const C g[16], bool end_left, bool is_swap);
+  __device__ void form_theta(int i, const C g[16], bool end_left, C* X);
+  __device__ int jacobi(C* X, int m, int nc);
+  // events
+  __device__ void apply_event(int k, int v, int& sign_count);
+  // measurement
+  __device__ void measure_z(double* out_v);
+};
+
+}  // namespace tepai

@@ -1,0 +1,21 @@
+// Instantiation of the ensemble kernel for float tensor arithmetic.
+#include "ensemble.cuh"
+
+namespace tepai {
+
+cudaError_t launch_ensemble_f32(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(ensemble_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  ensemble_kernel<float><<<grid, block, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t occupancy_ensemble_f32(int block, size_t smem, int* ctas_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(ensemble_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, ensemble_kernel<float>, block, smem);
+}
+
+}  // namespace tepai

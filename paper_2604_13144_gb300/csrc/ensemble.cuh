@@ -1,0 +1,293 @@
+// Sample initialisation, events, <Z_i> measurement and the persistent
+// ensemble kernel (one CTA per sample at a time, samples pulled from an
+// atomic work queue).
+#pragma once
+#include "qr.cuh"
+#include "svd_update.cuh"
+
+namespace tepai {
+
+template <typename R>
+__device__ void Engine<R>::init_product() {
+  for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = 1;
+  for (int i = tid(); i < a.n; i += nt()) {
+    C* p = S(i);
+    const int b = a.init_bits[i] ? 1 : 0;
+    p[0] = C{b == 0 ? R(1) : R(0), 0};
+    p[1] = C{b == 1 ? R(1) : R(0), 0};
+  }
+  centre = 0;
+  __syncthreads();
+}
+
+// Copy the shared initial tensors, bring them to right-canonical form with the
+// centre on site 0 (LQ sweep from the right), and normalise the state.
+template <typename R>
+__device__ void Engine<R>::init_from_tensors() {
+  for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = a.init_dims[i];
+  __syncthreads();
+  size_t off = 0;
+  for (int i = 0; i < a.n; ++i) {
+    const int cnt = sm.dims[i] * 2 * sm.dims[i + 1];
+    C* p = S(i);
+    for (int e = tid(); e < cnt; e += nt())
+      p[e] = C{(R)a.init_tensors[2 * (off + e)], (R)a.init_tensors[2 * (off + e) + 1]};
+    off += cnt;
+  }
+  centre = a.n - 1;
+  __syncthreads();
+  move_centre(0);
+  const int cnt = 2 * sm.dims[1];
+  double s2 = 0.0;
+  for (int e = tid(); e < cnt; e += nt()) s2 += (double)abs2(S(0)[e]);
+  s2 = block_sum(s2, sm.red);
+  const R inv = (R)(1.0 / sqrt(s2));
+  for (int e = tid(); e < cnt; e += nt()) S(0)[e] = scale(S(0)[e], inv);
+  __syncthreads();
+}
+
+template <typename R>
+__device__ void Engine<R>::apply_1site(int i, const C u[4]) {
+  const int dl = sm.dims[i], dr = sm.dims[i + 1];
+  C* p = S(i);
+  for (int e = tid(); e < dl * dr; e += nt()) {
+    const int aa = e / dr, bb = e - aa * dr;
+    C* x0p = p + (size_t)(aa * 2) * dr + bb;
+    C* x1p = x0p + dr;
+    const C x0 = *x0p, x1 = *x1p;
+    C y0 = {0, 0}, y1 = {0, 0};
+    fma_c(y0, u[0], x0); fma_c(y0, u[1], x1);
+    fma_c(y1, u[2], x0); fma_c(y1, u[3], x1);
+    *x0p = y0; *x1p = y1;
+  }
+  __syncthreads();
+}
+
+template <typename R> __device__ __forceinline__ void pauli2(int p, cplx<R> u[4]) {
+  if (p == 0) { u[0] = {0, 0}; u[1] = {1, 0}; u[2] = {1, 0}; u[3] = {0, 0}; }
+  else if (p == 1) { u[0] = {0, 0}; u[1] = {0, -1}; u[2] = {0, 1}; u[3] = {0, 0}; }
+  else { u[0] = {1, 0}; u[1] = {0, 0}; u[2] = {0, 0}; u[3] = {-1, 0}; }
+}
+
+// Event (j, k, v): v = 1 setting B, 2 setting C, 3 deterministic Trotter gate.
+// Setting C is R_k(pi) = -i h_k, applied as the Pauli string h_k (the global
+// phase drops out of every expectation value) and flips sign(g_l) (App. B).
+// A two-site rotation on the ring bond (n-1, 0) is routed: site n-1 is swapped
+// left to position 1, the gate acts on chain bond (0, 1), and the site is
+// swapped back; every swap is a truncated two-site update.
+template <typename R>
+__device__ void Engine<R>::apply_event(int k, int v, int& sign_count) {
+  const TermDev& T = a.terms[k];
+  if (tid() == 0) st.events++;
+  if (v == 2) sign_count++;
+  if (T.kind == 0) {
+    C u[4];
+    if (v == 2) pauli2<R>(2, u);
+    else for (int q = 0; q < 4; ++q) u[q] = C{(R)T.g[2 * q], (R)T.g[2 * q + 1]};
+    apply_1site(T.a, u);
+    return;
+  }
+  if (v == 2) {
+    C u[4];
+    pauli2<R>(T.pauli, u);
+    apply_1site(T.a, u);
+    apply_1site(T.b, u);
+    return;
+  }
+  C g[16];
+  for (int q = 0; q < 16; ++q) g[q] = C{(R)T.g[2 * q], (R)T.g[2 * q + 1]};
+  if (T.b == T.a + 1) { two_site(T.a, g, false, false); return; }
+  // ring bond: T.a == n-1, T.b == 0
+  C sw[16];
+  for (int q = 0; q < 16; ++q) sw[q] = C{0, 0};
+  sw[0] = C{1, 0}; sw[6] = C{1, 0}; sw[9] = C{1, 0}; sw[15] = C{1, 0};
+  const int n = a.n;
+  for (int p = n - 2; p >= 1; --p) two_site(p, sw, true, true);
+  // chain bond (0, 1) holds (site 0, site n-1): reorder the gate basis
+  C g2[16];
+  for (int st4 = 0; st4 < 4; ++st4)
+    for (int q = 0; q < 4; ++q) {
+      const int st_sw = ((st4 & 1) << 1) | (st4 >> 1), q_sw = ((q & 1) << 1) | (q >> 1);
+      g2[st4 * 4 + q] = g[st_sw * 4 + q_sw];
+    }
+  two_site(0, g2, false, false);
+  for (int p = 1; p <= n - 2; ++p) two_site(p, sw, false, true);
+}
+
+// <Z_i> / <psi|psi> for all sites. With the centre on site c, sites left of c
+// are left-orthonormal and sites right of c are right-orthonormal, so a
+// transfer-matrix sweep rightward from c (E <- sum_s A^s^H E A^s) gives
+// <Z_i> for i >= c and a sweep leftward from c (F <- sum_s A^s F A^s^H) gives
+// <Z_i> for i < c.
+template <typename R>
+__device__ void Engine<R>::measure_z(double* zout) {
+  const int n = a.n, c = centre;
+  C* E = TH;
+  C* Tm = TH + (size_t)cap * cap;
+  double nrm = 1.0;
+  // rightward sweep
+  {
+    const int d = sm.dims[c];
+    for (int e = tid(); e < d * d; e += nt()) E[e] = C{(e / d == e % d) ? R(1) : R(0), 0};
+    __syncthreads();
+    for (int i = c; i < n; ++i) {
+      const int dl = sm.dims[i], dr = sm.dims[i + 1];
+      const C* A = S(i);
+      for (int e = tid(); e < 2 * dl * dr; e += nt()) {
+        const int s = e / (dl * dr), rem = e - s * dl * dr, aa = rem / dr, bb = rem - aa * dr;
+        C acc = {0, 0};
+        for (int q = 0; q < dl; ++q) fma_c(acc, E[(size_t)aa * dl + q], A[(size_t)(q * 2 + s) * dr + bb]);
+        Tm[e] = acc;
+      }
+      __syncthreads();
+      double zp = 0.0, np_ = 0.0;
+      for (int e = tid(); e < 2 * dl * dr; e += nt()) {
+        const int s = e / (dl * dr), rem = e - s * dl * dr, aa = rem / dr, bb = rem - aa * dr;
+        const C av = A[(size_t)(aa * 2 + s) * dr + bb];
+        const double re = (double)av.re * (double)Tm[e].re + (double)av.im * (double)Tm[e].im;
+        zp += s ? -re : re;
+        np_ += re;
+      }
+      const double z = block_sum(zp, sm.red);
+      const double nn = block_sum(np_, sm.red);
+      if (i == c) nrm = nn;
+      if (tid() == 0) sm.zval[i] = z;
+      if (i + 1 < n) {
+        for (int e = tid(); e < dr * dr; e += nt()) {
+          const int b1 = e / dr, b2 = e - b1 * dr;
+          C acc = {0, 0};
+          for (int s = 0; s < 2; ++s)
+            for (int q = 0; q < dl; ++q)
+              fma_cc(acc, A[(size_t)(q * 2 + s) * dr + b1], Tm[(size_t)s * dl * dr + (size_t)q * dr + b2]);
+          XG[e] = acc;
+        }
+        __syncthreads();
+        for (int e = tid(); e < dr * dr; e += nt()) E[e] = XG[e];
+        __syncthreads();
+      }
+    }
+  }
+  // leftward sweep
+  if (c > 0) {
+    const int d = sm.dims[c + 1];
+    for (int e = tid(); e < d * d; e += nt()) E[e] = C{(e / d == e % d) ? R(1) : R(0), 0};
+    __syncthreads();
+    for (int i = c; i >= 0; --i) {
+      const int dl = sm.dims[i], dr = sm.dims[i + 1];
+      const C* A = S(i);
+      // U^s[a][b'] = sum_b A[a][s][b] F[b][b']
+      for (int e = tid(); e < 2 * dl * dr; e += nt()) {
+        const int s = e / (dl * dr), rem = e - s * dl * dr, aa = rem / dr, bb = rem - aa * dr;
+        C acc = {0, 0};
+        const C* ar = A + (size_t)(aa * 2 + s) * dr;
+        for (int q = 0; q < dr; ++q) fma_c(acc, ar[q], E[(size_t)q * dr + bb]);
+        Tm[e] = acc;
+      }
+      __syncthreads();
+      if (i < c) {
+        double zp = 0.0;
+        for (int e = tid(); e < 2 * dl * dr; e += nt()) {
+          const int s = e / (dl * dr), rem = e - s * dl * dr, aa = rem / dr, bb = rem - aa * dr;
+          const C av = A[(size_t)(aa * 2 + s) * dr + bb];
+          const double re = (double)av.re * (double)Tm[e].re + (double)av.im * (double)Tm[e].im;
+          zp += s ? -re : re;
+        }
+        const double z = block_sum(zp, sm.red);
+        if (tid() == 0) sm.zval[i] = z;
+      }
+      if (i == 0) break;
+      // F'[a][a'] = sum_s sum_b' U^s[a][b'] conj(A[a'][s][b'])
+      for (int e = tid(); e < dl * dl; e += nt()) {
+        const int a1 = e / dl, a2 = e - a1 * dl;
+        C acc = {0, 0};
+        for (int s = 0; s < 2; ++s)
+          for (int q = 0; q < dr; ++q)
+            fma_cc(acc, A[(size_t)(a2 * 2 + s) * dr + q], Tm[(size_t)s * dl * dr + (size_t)a1 * dr + q]);
+        XG[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid(); e < dl * dl; e += nt()) E[e] = XG[e];
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int o = tid(); o < a.n_obs; o += nt()) zout[o] = sm.zval[a.obs[o]] / nrm;
+  __syncthreads();
+}
+
+// The TE-PAI sampler draw of gate (j, k) for global sample s: Philox4x64-10 with
+// key (seed, s) and counter (j, k, 0, 0); word 0 against floor(q_k 2^64) decides
+// "not A", word 1 against floor(r_k 2^64) decides C over B.
+__device__ __forceinline__ int draw_gate(const KArgs& a, unsigned long long s, long long j, int k) {
+  if (a.variant == 2) return 3;
+  const u64x4 x = philox4x64_10(u64x4{(unsigned long long)j, (unsigned long long)k, 0ull, 0ull}, a.seed, s);
+  const TermDev& T = a.terms[k];
+  if (x.x0 < T.thr_event) return (x.x1 < T.thr_c) ? 2 : 1;
+  return 0;
+}
+
+__device__ inline SmemLayout carve_smem(unsigned char* base, const KArgs& a, int csize) {
+  SmemLayout s;
+  size_t o = 0;
+  s.dims = reinterpret_cast<int*>(base + o); o += align_up((size_t)(a.n + 1) * 4, 16);
+  s.flags = base + o; o += align_up((size_t)a.L, 16);
+  s.red = reinterpret_cast<double*>(base + o); o += 64 * 8;
+  s.wn = reinterpret_cast<double*>(base + o); o += align_up((size_t)2 * a.chi_cap * 8, 16);
+  s.perm = reinterpret_cast<int*>(base + o); o += align_up((size_t)2 * a.chi_cap * 4, 16);
+  s.zval = reinterpret_cast<double*>(base + o); o += align_up((size_t)a.n * 8, 16);
+  s.ibuf = reinterpret_cast<int*>(base + o); o += 16 * 4;
+  s.dbuf = reinterpret_cast<double*>(base + o); o += 16 * 8;
+  s.hh = base + o; o += align_up((size_t)3 * 2 * a.chi_cap * csize, 16);
+  o = align_up(o, 128);
+  s.x = base + o;
+  return s;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) ensemble_kernel(const __grid_constant__ KArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ long long s_next;
+  SmemLayout sm = carve_smem(smem_raw, a, (int)sizeof(cplx<R>));
+  char* arena = a.arena + (size_t)blockIdx.x * a.arena_stride;
+  Engine<R> eng(a, sm, arena);
+  while (true) {
+    if (threadIdx.x == 0) s_next = (long long)atomicAdd(a.counter, 1ull);
+    __syncthreads();
+    const long long si = s_next;
+    __syncthreads();
+    if (si >= a.n_samples) break;
+    const unsigned long long s = (unsigned long long)(a.sample_offset + si);
+    if (a.init_tensors) eng.init_from_tensors(); else eng.init_product();
+    int sign_count = 0;
+    int mi = 0;
+    for (long long j = 1; j <= a.run_steps; ++j) {
+      for (int k = threadIdx.x; k < a.L; k += blockDim.x) sm.flags[k] = (unsigned char)draw_gate(a, s, j, k);
+      __syncthreads();
+      for (int k = 0; k < a.L; ++k) {
+        const int f = sm.flags[k];
+        if (f) eng.apply_event(k, f, sign_count);
+      }
+      __syncthreads();
+      while (mi < a.M && a.snaps[mi] == j) {
+        eng.measure_z(a.v + ((size_t)si * a.M + mi) * a.n_obs);
+        if (threadIdx.x == 0) a.sign[(size_t)si * a.M + mi] = (sign_count & 1) ? -1 : 1;
+        ++mi;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    const LocalStats& st = eng.st;
+    atomicAdd(&a.stats->events, st.events);
+    atomicAdd(&a.stats->gate_updates, st.gate_updates);
+    atomicAdd(&a.stats->swap_updates, st.swap_updates);
+    atomicAdd(&a.stats->qr_moves, st.qr_moves);
+    atomicAdd(&a.stats->sweeps, st.sweeps);
+    atomicAdd(&a.stats->not_converged, st.not_converged);
+    atomicMax(&a.stats->max_chi, st.max_chi);
+    atomicMax(reinterpret_cast<unsigned long long*>(&a.stats->max_discarded),
+              (unsigned long long)__double_as_longlong(st.max_discarded));
+    atomicAdd(&a.stats->alg_flops, st.alg_flops);
+  }
+}
+
+}  // namespace tepai

@@ -1,0 +1,148 @@
+// Host planner of the CUDA path (FP64): term list, rotation angles, PAI
+// coefficients, sampler thresholds, gate matrices and ||g(t_m)||_1.
+// Follows App. A.3 (Eq. productFormula, Eq. settings, Eq. gammas), App. A.4
+// (no-pi variant) and App. A.6 (Eq. overhead-bound).
+#pragma once
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/tepai.h"
+#include "common.cuh"
+
+namespace tepai {
+
+struct HostPlan {
+  int n = 0, L = 0, M = 0, n_obs = 0, periodic = 0;
+  long long N = 0, run_steps = 0;
+  std::vector<TermDev> terms;
+  std::vector<int> snaps;
+  std::vector<double> gnorm;
+  std::vector<int> obs;
+  std::vector<unsigned char> bits;
+  double gnorm_step = 1.0, expected_nu = 0.0;
+};
+
+inline bool finite_arr(const double* p, int n) {
+  if (!p) return false;
+  for (int i = 0; i < n; ++i) if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// floor(p * 2^64), saturated: a uniform 64-bit word x selects the event when
+// x < threshold, so the event probability is threshold / 2^64.
+inline unsigned long long threshold_u64(double p) {
+  if (!(p > 0.0)) return 0ull;
+  const double v = std::ldexp(p, 64);
+  if (v >= 18446744073709551616.0) return ~0ull;
+  return (unsigned long long)std::floor(v);
+}
+
+// Pauli rotation R(phi) = exp(-i phi P/2) = cos(phi/2) I - i sin(phi/2) P for a
+// Pauli string P with P^2 = I, written into TermDev::g.
+inline void rotation_gate(int pauli, bool two_site, double phi, double* g) {
+  using cd = std::complex<double>;
+  cd P1[2][2];
+  if (pauli == 0) { P1[0][0] = 0; P1[0][1] = 1; P1[1][0] = 1; P1[1][1] = 0; }
+  else if (pauli == 1) { P1[0][0] = 0; P1[0][1] = cd(0, -1); P1[1][0] = cd(0, 1); P1[1][1] = 0; }
+  else { P1[0][0] = 1; P1[0][1] = 0; P1[1][0] = 0; P1[1][1] = -1; }
+  const double c = std::cos(phi / 2), s = std::sin(phi / 2);
+  const int d = two_site ? 4 : 2;
+  for (int r = 0; r < d; ++r)
+    for (int q = 0; q < d; ++q) {
+      cd p;
+      if (two_site) p = P1[r >> 1][q >> 1] * P1[r & 1][q & 1];
+      else p = P1[r][q];
+      const cd v = (r == q ? cd(c, 0) : cd(0, 0)) - cd(0, s) * p;
+      g[2 * (r * d + q)] = v.real();
+      g[2 * (r * d + q) + 1] = v.imag();
+    }
+}
+
+inline int build_plan(const tepai_problem* P, const tepai_params* Q, HostPlan& hp) {
+  if (!P || !Q) return TEPAI_ERR_INVALID_ARG;
+  const int n = P->n;
+  if (n < 2) return TEPAI_ERR_INVALID_ARG;
+  const int nb = P->periodic ? n : n - 1;
+  if (!finite_arr(P->Jx, nb) || !finite_arr(P->Jy, nb) || !finite_arr(P->Jz, nb) || !finite_arr(P->h, n))
+    return TEPAI_ERR_INVALID_ARG;
+  if (!P->init_bits) return TEPAI_ERR_INVALID_ARG;
+  if (!(std::isfinite(Q->T) && Q->T >= 0.0) || Q->n_steps < 1) return TEPAI_ERR_INVALID_ARG;
+  if (!(std::isfinite(Q->delta) && Q->delta > 0.0)) return TEPAI_ERR_INVALID_ARG;
+  if (Q->chi_max < 1 || !(std::isfinite(Q->cutoff) && Q->cutoff >= 0.0)) return TEPAI_ERR_INVALID_ARG;
+  if (Q->variant < 0 || Q->variant > 2 || Q->precision < 0 || Q->precision > 1) return TEPAI_ERR_INVALID_ARG;
+  if (Q->n_samples < 0 || Q->sample_offset < 0) return TEPAI_ERR_INVALID_ARG;
+  const long long S = Q->run_steps ? Q->run_steps : Q->n_steps;
+  if (S < 1 || S > Q->n_steps) return TEPAI_ERR_INVALID_ARG;
+  if (Q->n_snapshots < 1 || S % Q->n_snapshots != 0) return TEPAI_ERR_INVALID_ARG;
+  hp = HostPlan();
+  hp.n = n; hp.periodic = P->periodic ? 1 : 0; hp.N = Q->n_steps; hp.run_steps = S; hp.M = Q->n_snapshots;
+  if (Q->obs_sites) {
+    if (Q->n_obs < 1) return TEPAI_ERR_INVALID_ARG;
+    for (int o = 0; o < Q->n_obs; ++o) {
+      if (Q->obs_sites[o] < 0 || Q->obs_sites[o] >= n) return TEPAI_ERR_INVALID_ARG;
+      hp.obs.push_back(Q->obs_sites[o]);
+    }
+  } else {
+    for (int i = 0; i < n; ++i) hp.obs.push_back(i);
+  }
+  hp.n_obs = (int)hp.obs.size();
+  for (int i = 0; i < n; ++i) hp.bits.push_back(P->init_bits[i] ? 1 : 0);
+  // term list: Z_0..Z_{n-1}, then per bond b: XX_b, YY_b, ZZ_b
+  struct T0 { int kind, a, b, pauli; double c; };
+  std::vector<T0> tl;
+  for (int i = 0; i < n; ++i) tl.push_back({0, i, i, 2, P->h[i]});
+  for (int b = 0; b < nb; ++b) {
+    const int sa = b, sb = (b + 1) % n;
+    tl.push_back({1, sa, sb, 0, P->Jx[b]});
+    tl.push_back({1, sa, sb, 1, P->Jy[b]});
+    tl.push_back({1, sa, sb, 2, P->Jz[b]});
+  }
+  hp.L = (int)tl.size();
+  const double delta = Q->delta;
+  double sumq = 0.0, gstep = 1.0;
+  for (const T0& t : tl) {
+    TermDev td{};
+    td.kind = t.kind; td.a = t.a; td.b = t.b; td.pauli = t.pauli;
+    const double th = 2.0 * t.c * Q->T / (double)Q->n_steps;
+    double q, r, gn, phi;
+    if (Q->variant == TEPAI_TROTTER) {
+      q = 1.0; r = 0.0; gn = 1.0; phi = th;
+    } else {
+      if (std::fabs(th) > delta || delta > M_PI) return TEPAI_ERR_THETA_EXCEEDS_DELTA;
+      double g1, g2, g3;
+      if (Q->variant == TEPAI_NO_PI) {
+        const double lam = std::fabs(th) / delta;
+        g1 = 1.0 - lam; g2 = lam; g3 = 0.0;
+      } else {
+        const double ta = std::fabs(th);
+        g1 = std::cos(ta / 2) * std::sin(delta / 2 - ta / 2) / std::sin(delta / 2);
+        g2 = std::sin(ta) / std::sin(delta);
+        g3 = -std::sin(ta / 2) * std::sin(delta / 2 - ta / 2) / std::cos(delta / 2);
+      }
+      const double a1 = std::fabs(g1), a2 = std::fabs(g2), a3 = std::fabs(g3);
+      gn = a1 + a2 + a3;
+      const double nonid = a2 + a3;
+      q = nonid / gn;
+      r = nonid > 0.0 ? a3 / nonid : 0.0;
+      phi = th != 0.0 ? std::copysign(delta, th) : delta;
+    }
+    td.thr_event = threshold_u64(q);
+    td.thr_c = threshold_u64(r);
+    rotation_gate(t.pauli, t.kind == 1, phi, td.g);
+    hp.terms.push_back(td);
+    sumq += q;
+    gstep *= gn;
+  }
+  hp.gnorm_step = gstep;
+  hp.expected_nu = (double)S * sumq;
+  for (int m = 1; m <= hp.M; ++m) {
+    const long long j = (long long)m * S / hp.M;
+    hp.snaps.push_back((int)j);
+    hp.gnorm.push_back(std::pow(gstep, (double)j));
+  }
+  return TEPAI_OK;
+}
+
+}  // namespace tepai

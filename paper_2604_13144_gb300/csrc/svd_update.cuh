@@ -1,0 +1,236 @@
+// Two-site update of the mixed-canonical MPS (Sec. II.A): theta contraction,
+// Pauli-rotation gate, one-sided Jacobi SVD, truncation to chi_max / cutoff,
+// renormalisation and write-back of the two site tensors.
+#pragma once
+#include "engine.cuh"
+
+namespace tepai {
+
+// theta'[(a,s),(t,b)] = sum_{s't'} g[st][s't'] sum_c A_i[a,s',c] A_{i+1}[c,t',b].
+// TH receives theta' row-major (2dl x 2dr). X receives the matrix whose columns
+// the SVD orthogonalises, column-major: theta' itself when the centre ends on
+// the right site, theta'^T when it ends on the left site.
+template <typename R>
+__device__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, C* X) {
+  const int dl = sm.dims[i], dc = sm.dims[i + 1], dr = sm.dims[i + 2];
+  const C* A = S(i);
+  const C* B = S(i + 1);
+  const int m = 2 * dl, ncol = 2 * dr;
+  for (int e = tid(); e < dl * dr; e += nt()) {
+    const int aa = e / dr, bb = e - aa * dr;
+    C t[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    const C* a0p = A + (size_t)(aa * 2) * dc;
+    const C* a1p = a0p + dc;
+    for (int c = 0; c < dc; ++c) {
+      const C a0 = a0p[c], a1 = a1p[c];
+      const C b0 = B[(size_t)(c * 2) * dr + bb], b1 = B[(size_t)(c * 2 + 1) * dr + bb];
+      fma_c(t[0], a0, b0); fma_c(t[1], a0, b1); fma_c(t[2], a1, b0); fma_c(t[3], a1, b1);
+    }
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4) {
+      C o = {0, 0};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) fma_c(o, g[s4 * 4 + q], t[q]);
+      const int row = aa * 2 + (s4 >> 1), col = (s4 & 1) * dr + bb;
+      TH[(size_t)row * ncol + col] = o;
+      if (end_left) X[(size_t)row * ncol + col] = o;
+      else X[(size_t)col * m + row] = o;
+    }
+  }
+  __syncthreads();
+}
+
+// Cyclic one-sided Jacobi (Hestenes) on the columns of X (m x nc, column-major),
+// in parallel round-robin order: every round pairs all columns disjointly, one
+// warp per pair; a sweep is nc-1 rounds. A pair (p,q) is rotated when
+// |x_p^H x_q| > tol * |x_p| |x_q|. The complex rotation first removes the phase
+// of x_p^H x_q from x_q, then applies the real Jacobi rotation that zeroes the
+// off-diagonal of the 2x2 Gram matrix. Returns the sweeps run; ibuf[1] = 1
+// when the last sweep rotated nothing (converged).
+template <typename R>
+__device__ int Engine<R>::jacobi(C* X, int m, int nc) {
+  const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
+  const int np = nc + (nc & 1);
+  const R tol = (R)a.tol;
+  int sweep = 0;
+  if (tid() == 0) sm.ibuf[1] = 0;
+  if (nc < 2) { __syncthreads(); if (tid() == 0) sm.ibuf[1] = 1; __syncthreads(); return 0; }
+  while (sweep < a.max_sweeps) {
+    if (tid() == 0) sm.ibuf[0] = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int t = w; t < np / 2; t += nw) {
+        int p, q;
+        if (t == 0) { p = np - 1; q = r; }
+        else { p = (r + t) % (np - 1); q = (r - t + np - 1) % (np - 1); }
+        if (p >= nc || q >= nc) continue;
+        C* xp = X + (size_t)p * m;
+        C* xq = X + (size_t)q * m;
+        R al = 0, be = 0, gr = 0, gi = 0;
+        for (int row = lane; row < m; row += 32) {
+          const C u = xp[row], v = xq[row];
+          al = fma(u.re, u.re, fma(u.im, u.im, al));
+          be = fma(v.re, v.re, fma(v.im, v.im, be));
+          gr = fma(u.re, v.re, fma(u.im, v.im, gr));
+          gi = fma(u.re, v.im, fma(-u.im, v.re, gi));
+        }
+        al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+        const R g = sqrt(gr * gr + gi * gi);
+        if (!(g > tol * sqrt(al * be))) continue;
+        const R zeta = (be - al) / (R(2) * g);
+        const R az = fabs(zeta);
+        R tt = az > R(1) ? R(1) / (az * (R(1) + sqrt(R(1) + R(1) / (az * az))))
+                         : R(1) / (az + sqrt(R(1) + az * az));
+        if (zeta < R(0)) tt = -tt;
+        const R c = rsqrt_<R>(R(1) + tt * tt), s = c * tt;
+        const C e = {gr / g, -gi / g};  // e^{-i phi}
+        for (int row = lane; row < m; row += 32) {
+          const C u = xp[row], v0 = xq[row];
+          const C v = mul(e, v0);
+          xp[row] = C{c * u.re - s * v.re, c * u.im - s * v.im};
+          xq[row] = C{s * u.re + c * v.re, s * u.im + c * v.im};
+        }
+        if (lane == 0) atomicAdd(&sm.ibuf[0], 1);
+      }
+      __syncthreads();
+    }
+    ++sweep;
+    const int rot = sm.ibuf[0];
+    __syncthreads();
+    if (rot == 0) { if (tid() == 0) sm.ibuf[1] = 1; break; }
+  }
+  __syncthreads();
+  return sweep;
+}
+
+// Gate on bond (i, i+1). The centre is first moved onto site i or i+1, so that
+// theta holds it and the environments are orthonormal (mixed-canonical form).
+// After the SVD the centre sits on site i (end_left) or i+1.
+// Truncation keeps k = max(1, min(chi_max, k_floor, k_cut, min(m, nc))) sorted
+// singular values (descending, ties by column index):
+//   k_cut   = the smallest k with sum_{j>=k} s_j^2 <= cutoff * sum_j s_j^2,
+//   k_floor = #{j : s_j > floor_rel * s_0};
+// then, if s_{k-1} - s_k <= gap_rel * s_0, k drops to the largest k' < k with a
+// clear gap (a cut never splits a group of equal singular values), unless no
+// such k' >= 1 exists.
+// The kept values are rescaled to unit norm, so every sample stays normalised.
+template <typename R>
+__device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is_swap) {
+  if (centre < i) move_centre(i);
+  else if (centre > i + 1) move_centre(i + 1);
+  const int dl = sm.dims[i], dc = sm.dims[i + 1], dr = sm.dims[i + 2];
+  const int m = end_left ? 2 * dr : 2 * dl;
+  const int nc = end_left ? 2 * dl : 2 * dr;
+  C* X = (a.x_in_smem && m * nc <= a.smem_x_elems) ? reinterpret_cast<C*>(sm.x) : XG;
+  form_theta(i, g, end_left, X);
+  const int sweeps = jacobi(X, m, nc);
+  const int converged = sm.ibuf[1];
+  const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
+  // squared column norms (FP64 accumulation)
+  for (int col = w; col < nc; col += nw) {
+    const C* x = X + (size_t)col * m;
+    double s2 = 0.0;
+    for (int row = lane; row < m; row += 32) s2 += (double)abs2(x[row]);
+    s2 = warp_sum(s2);
+    if (lane == 0) sm.wn[col] = s2;
+  }
+  __syncthreads();
+  for (int j = tid(); j < nc; j += nt()) {
+    const double wj = sm.wn[j];
+    int rank = 0;
+    for (int q = 0; q < nc; ++q) {
+      const double wq = sm.wn[q];
+      rank += (wq > wj) || (wq == wj && q < j);
+    }
+    sm.perm[rank] = j;
+  }
+  __syncthreads();
+  if (tid() == 0) {
+    double tot = 0.0;
+    for (int j = nc - 1; j >= 0; --j) tot += sm.wn[sm.perm[j]];
+    const double thr = a.cutoff * tot;
+    int kcut = nc;
+    double acc = 0.0;
+    for (int j = nc - 1; j >= 1; --j) {
+      acc += sm.wn[sm.perm[j]];
+      if (acc <= thr) kcut = j; else break;
+    }
+    const double s0 = sqrt(sm.wn[sm.perm[0]]);
+    int kfloor = 0;
+    while (kfloor < nc && sqrt(sm.wn[sm.perm[kfloor]]) > a.floor_rel * s0) ++kfloor;
+    int k = min(min(cap, kfloor), min(kcut, min(m, nc)));
+    if (k < 1) k = 1;
+    // never split a group of equal singular values: drop the whole group
+    if (k < nc && sqrt(sm.wn[sm.perm[k]]) > a.floor_rel * s0) {
+      int kk = k;
+      while (kk >= 1 && sqrt(sm.wn[sm.perm[kk - 1]]) - sqrt(sm.wn[sm.perm[kk]]) <= a.gap_rel * s0) --kk;
+      if (kk >= 1) k = kk;
+    }
+    double kept = 0.0;
+    for (int j = k - 1; j >= 0; --j) kept += sm.wn[sm.perm[j]];
+    sm.ibuf[2] = k;
+    sm.dbuf[0] = kept > 0.0 ? 1.0 / sqrt(kept) : 0.0;
+    const double disc = tot > 0.0 ? (tot - kept) / tot : 0.0;
+    if (disc > st.max_discarded) st.max_discarded = disc;
+    if (k > st.max_chi) st.max_chi = k;
+    st.sweeps += sweeps;
+    if (!converged) st.not_converged++;
+    if (is_swap) st.swap_updates++; else st.gate_updates++;
+    const double mx = (double)max(m, nc), mn = (double)min(m, nc);
+    st.alg_flops += 32.0 * dl * dc * dr + 4.0 * (14.0 * mx * mn * mn + 8.0 * mn * mn * mn);
+  }
+  __syncthreads();
+  const int k = sm.ibuf[2];
+  const R renorm = (R)sm.dbuf[0];
+  if (!end_left) {
+    // site i <- U[:, :k] (2dl x k); site i+1 <- renorm * U^H theta' (k x 2dr)
+    C* Ai = S(i);
+    for (int e = tid(); e < m * k; e += nt()) {
+      const int row = e / k, mm = e - row * k;
+      const int col = sm.perm[mm];
+      const double wv = sm.wn[col];
+      const R inv = wv > 0.0 ? (R)(1.0 / sqrt(wv)) : R(0);
+      Ai[e] = scale(X[(size_t)col * m + row], inv);
+    }
+    __syncthreads();
+    C* Bi = S(i + 1);
+    const int ncol = 2 * dr;
+    for (int e = tid(); e < k * ncol; e += nt()) {
+      const int mm = e / ncol, col = e - mm * ncol;
+      C acc2 = {0, 0};
+      for (int row = 0; row < m; ++row) fma_cc(acc2, Ai[(size_t)row * k + mm], TH[(size_t)row * ncol + col]);
+      Bi[e] = scale(acc2, renorm);
+    }
+    __syncthreads();
+    if (tid() == 0) sm.dims[i + 1] = k;
+    centre = i + 1;
+  } else {
+    // site i+1 <- V^H[:k, :] (k x 2dr); site i <- renorm * theta' V (2dl x k)
+    C* Bi = S(i + 1);
+    const int ncol = 2 * dr;  // == m
+    for (int e = tid(); e < k * ncol; e += nt()) {
+      const int mm = e / ncol, col = e - mm * ncol;
+      const int src = sm.perm[mm];
+      const double wv = sm.wn[src];
+      const R inv = wv > 0.0 ? (R)(1.0 / sqrt(wv)) : R(0);
+      Bi[e] = scale(X[(size_t)src * m + col], inv);
+    }
+    __syncthreads();
+    C* Ai = S(i);
+    const int rows = 2 * dl;
+    for (int e = tid(); e < rows * k; e += nt()) {
+      const int row = e / k, mm = e - row * k;
+      C acc2 = {0, 0};
+      const C* th = TH + (size_t)row * ncol;
+      const C* bv = Bi + (size_t)mm * ncol;
+      for (int col = 0; col < ncol; ++col) fma_cc(acc2, bv[col], th[col]);
+      Ai[e] = scale(acc2, renorm);
+    }
+    __syncthreads();
+    if (tid() == 0) sm.dims[i + 1] = k;
+    centre = i;
+  }
+  __syncthreads();
+}
+
+}  // namespace tepai

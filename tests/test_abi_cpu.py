@@ -1,0 +1,71 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and its FP64 host planner agrees with the oracle's."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import planner
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2604_13144_gb300 import build
+    build.build()
+    from paper_2604_13144_gb300 import tepai
+    return tepai
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tepai.h")).read()
+    return sorted(set(re.findall(r"\b(tepai_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(T):
+    names = _declared()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(T._lib, name), name
+    assert set(T.EXPORTED) == set(names)
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
+def test_host_planner_matches_oracle(T, cfg):
+    prob, par, _ = W.config(cfg)
+    g, nu = T.tepai_gnorm(prob, par)
+    plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, par.variant)
+    snaps = planner.snapshot_steps(par.n_steps, par.n_snapshots)
+    want = np.array([planner.gnorm_at(plan, j) for j in snaps])
+    assert np.allclose(g, want, rtol=1e-13, atol=0)
+    assert abs(nu - planner.expected_nu(plan, par.n_steps)) <= 1e-9 * nu
+
+
+def test_invalid_arguments_are_rejected(T):
+    prob, par, _ = W.config(1)
+    bad = W.Params(**{**par.__dict__, "n_steps": 100})      # theta = 0.02 > Delta = pi/256
+    with pytest.raises(T.TepaiError) as e:
+        T.tepai_gnorm(prob, bad)
+    assert e.value.code == 2
+    bad = W.Params(**{**par.__dict__, "n_snapshots": 7})    # 7 does not divide 2000
+    with pytest.raises(T.TepaiError) as e:
+        T.tepai_gnorm(prob, bad)
+    assert e.value.code == 1
+    p2 = W.spin_ring(8, 1.0)
+    p2.h = p2.h.copy()
+    p2.h[3] = float("nan")
+    with pytest.raises(T.TepaiError):
+        T.tepai_gnorm(p2, par)
+    trot = W.Params(**{**par.__dict__, "n_steps": 100, "variant": 2})   # Trotter has no Delta bound
+    g, nu = T.tepai_gnorm(prob, trot)
+    assert np.all(g == 1.0) and nu == 100 * 32
+
+
+def test_no_pi_gnorm_is_one(T):
+    prob, par, _ = W.config(2)
+    g, _ = T.tepai_gnorm(prob, W.Params(**{**par.__dict__, "variant": 1}))
+    assert np.all(np.abs(g - 1.0) < 1e-15)

@@ -1,0 +1,188 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle on the same
+seeded circuits. Tolerances: 1e-10 on every <Z_i> in FP64 mode and 1e-4 in
+mixed mode; the sampler and the signs are bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import estimator, planner, sampler
+from oracle import run as oracle_run
+from oracle import statevector as sv
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOLMIX = 1e-10, 1e-4
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2604_13144_gb300 import build
+    build.build()
+    from paper_2604_13144_gb300 import tepai
+    return tepai
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    c = T.tepai_create(0)
+    yield c
+    T.tepai_destroy(c)
+
+
+def P(**kw):
+    base = dict(T=0.5, n_steps=200, delta=math.pi / 64, n_samples=4, chi_max=8, cutoff=0.0,
+                n_snapshots=4, seed=1, precision=0)
+    base.update(kw)
+    return W.Params(**base)
+
+
+# ------------------------------------------------------------------ sampler
+@pytest.mark.parametrize("cfg,variant", [(1, 0), (2, 0), (3, 0), (2, 1)])
+def test_device_sampler_matches_oracle(T, ctx, cfg, variant):
+    prob, par, _ = W.config(cfg)
+    par = W.Params(**{**par.__dict__, "variant": variant})
+    plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, variant)
+    for s in (0, 1, 12345):
+        want = sampler.sample_events(plan, par.seed, s, par.n_steps)
+        got = T.tepai_export_circuit(ctx, prob, par, s)
+        assert got.shape == want.shape and np.array_equal(got, want), (cfg, s)
+
+
+# ------------------------------------------------------------------ FP64 parity
+def _compare(T, ctx, prob, par, tol, init=None, use_sv=False):
+    got = T.tepai_sample_values(ctx, prob, par, init)
+    # truncation-rule parameters of the library's precision mode
+    floor_rel, gap_rel = (1e-14, 1e-12) if par.precision == 0 else (4e-6, 1e-5)
+    ref = oracle_run.run(prob, par, init_tensors=None if init is None else init[0],
+                         use_statevector=use_sv, floor_rel=floor_rel, gap_rel=gap_rel)
+    err = float(np.max(np.abs(got["v"] - ref["v"])))
+    assert np.array_equal(got["sign"], ref["sign"])
+    assert err <= tol, err
+    return got, ref, err
+
+
+def test_fp64_untruncated_matches_oracle_mps_and_statevector(T, ctx):
+    prob = W.spin_ring(6, 1.0, seed=0)
+    par = P(n_samples=6)
+    _compare(T, ctx, prob, par, TOL64)
+    _compare(T, ctx, prob, par, TOL64, use_sv=True)
+
+
+def test_fp64_trotter_mode_config1_matches_statevector(T, ctx):
+    prob, par, ex = W.config(1)
+    par = W.Params(**{**par.__dict__, "n_steps": ex["trotter_steps"], "variant": 2, "n_samples": 1,
+                      "obs_sites": None})
+    got, ref, _ = _compare(T, ctx, prob, par, TOL64, use_sv=True)
+    assert np.max(np.abs(got["v"].sum(axis=2))) < 1e-10       # sum_i <Z_i> conserved
+
+
+def test_fp64_config1_samples_match_statevector(T, ctx):
+    prob, par, _ = W.config(1)
+    par = W.Params(**{**par.__dict__, "n_samples": 3, "obs_sites": None})
+    _compare(T, ctx, prob, par, TOL64, use_sv=True)
+
+
+def test_fp64_truncated_matches_oracle(T, ctx):
+    prob = W.spin_ring(10, 1.0, seed=3)
+    par = P(n_samples=4, chi_max=6, cutoff=1e-9, T=1.0, n_steps=400, delta=math.pi / 32)
+    got, ref, _ = _compare(T, ctx, prob, par, TOL64)
+    assert max(s["max_chi"] for s in ref["stats"]) == 6
+
+
+def test_fp64_from_random_mps_matches_oracle(T, ctx):
+    prob = W.spin_ring(8, 1.0, seed=5)
+    tens, dims = W.random_mps_tensors(8, 8, seed=11)
+    par = P(n_samples=3, chi_max=8, cutoff=0.0, T=0.2, n_steps=80, delta=math.pi / 64)
+    _compare(T, ctx, prob, par, TOL64, init=(tens, dims))
+
+
+@pytest.mark.parametrize("n,periodic", [(2, True), (2, False), (3, True), (5, False)])
+def test_fp64_small_chains_and_rings(T, ctx, n, periodic):
+    prob = W.spin_ring(n, 1.0, seed=n, periodic=periodic)
+    _compare(T, ctx, prob, P(n_samples=3, chi_max=4), TOL64, use_sv=True)
+
+
+def test_fp64_chi_one_and_subsets(T, ctx):
+    prob = W.spin_ring(7, 1.0, seed=2)
+    par = P(n_samples=2, chi_max=1, run_steps=100, n_snapshots=5,
+            obs_sites=np.array([6, 0, 3], dtype=np.int32))
+    _compare(T, ctx, prob, par, TOL64)
+
+
+def test_no_pi_variant_fp64(T, ctx):
+    prob = W.spin_ring(6, 1.0, seed=4)
+    got, ref, _ = _compare(T, ctx, prob, P(n_samples=3, variant=1), TOL64)
+    assert np.all(got["sign"] == 1)
+
+
+# ------------------------------------------------------------------ mixed precision
+def test_mixed_truncated_matches_oracle(T, ctx):
+    prob = W.spin_ring(12, 2.0, seed=0)
+    par = P(n_samples=4, chi_max=16, cutoff=1e-10, T=1.0, n_steps=400, delta=math.pi / 64,
+            precision=1)
+    _compare(T, ctx, prob, par, TOLMIX)
+
+
+def test_mixed_config1_matches_statevector(T, ctx):
+    prob, par, _ = W.config(1)
+    par = W.Params(**{**par.__dict__, "n_samples": 2, "precision": 1, "obs_sites": None})
+    _compare(T, ctx, prob, par, TOLMIX, use_sv=True)
+
+
+# ------------------------------------------------------------------ estimator
+def test_ensemble_reduction_matches_oracle_estimator(T, ctx):
+    prob = W.spin_ring(6, 1.0, seed=7)
+    par = P(n_samples=64, T=1.0, n_steps=200, delta=math.pi / 16, n_snapshots=2)
+    vals = T.tepai_sample_values(ctx, prob, par)
+    res = T.tepai_run(ctx, prob, par)
+    g, _ = T.tepai_gnorm(prob, par)
+    mean, se, part = estimator.estimate(vals["v"], vals["sign"], g)
+    assert np.allclose(res["mean"], mean, rtol=1e-13, atol=1e-15)
+    assert np.allclose(res["stderr"], se, rtol=1e-12, atol=1e-15)
+    assert np.allclose(res["partials"][..., 0] + res["partials"][..., 1], part[..., 0] + part[..., 1],
+                       rtol=1e-13, atol=1e-13)
+    ref = oracle_run.run(prob, par)
+    assert np.max(np.abs(res["mean"] - ref["mean"])) < TOL64
+    assert np.any(vals["sign"] == -1)
+
+
+def test_results_independent_of_grid(T, ctx):
+    prob = W.spin_ring(6, 1.0, seed=8)
+    par = P(n_samples=12, precision=1)
+    a = T.DeviceRun(prob, par, grid_ctas=1)
+    b = T.DeviceRun(prob, par, grid_ctas=5)
+    import torch
+    va = torch.zeros((12, 4, 6), dtype=torch.float64, device="cuda")
+    vb = torch.zeros_like(va)
+    a.execute(v=va)
+    b.execute(v=vb)
+    torch.cuda.synchronize()
+    assert torch.equal(va, vb)
+    assert torch.equal(a.mean, b.mean)
+
+
+# ------------------------------------------------------------------ full-size bench workload
+def test_bench_workload_sampled_parity(T):
+    """The launch bench.py times (chi = 128, n = 64, batch = 2 per SM, shared random
+    MPS at the cap): sampled samples of the batch against the oracle, one by one."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    batch = 2 * sms
+    prob, par, init = W.bench_workload(batch, window_steps=1, sample_offset=777)
+    run = T.DeviceRun(prob, par, init)
+    v = torch.zeros((batch, 1, prob.n), dtype=torch.float64, device="cuda")
+    sg = torch.zeros((batch, 1), dtype=torch.int8, device="cuda")
+    run.execute(v=v, sign=sg)
+    torch.cuda.synchronize()
+    st = run.stats()
+    assert st["max_chi"] == 128 and st["n_not_converged"] == 0
+    v = v.cpu().numpy()
+    sg = sg.cpu().numpy()
+    for si in (0, batch - 1):
+        ref = oracle_run.run(prob, par, init_tensors=init[0], floor_rel=4e-6, gap_rel=1e-5,
+                             samples=[777 + si])
+        err = float(np.max(np.abs(v[si] - ref["v"][0])))
+        assert err <= TOLMIX, (si, err)
+        assert sg[si, 0] == ref["sign"][0, 0]

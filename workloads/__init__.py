@@ -137,3 +137,23 @@ def config(idx: int) -> tuple[Problem, Params, dict]:
                      seed=0, precision=1)
         return prob, par, {"name": "ring64_hybrid_T2to5", "t0": 2.0}
     raise ValueError(idx)
+
+
+# --------------------------------------------------------------------------
+# Benchmark workload: steady state at chi = 128.
+# Configuration 3's ring (n = 64 XXZ, Jz = 0.5, h ~ U[-1, 1], T = 3,
+# Delta = pi/1024, N = 18000, chi_max = 128, cutoff 1e-10). Every sample starts
+# from one shared random MPS whose bonds are already at the cap, so that every
+# two-site update runs at chi = 128. Each sample then evolves a window of the
+# first `window_steps` Trotter steps of its own TE-PAI circuit and is measured
+# once at the end of the window.
+# --------------------------------------------------------------------------
+
+def bench_workload(n_samples: int, window_steps: int = 2, sample_offset: int = 0,
+                   chi: int = 128, mps_seed: int = 1234):
+    prob, par, extra = config(3)
+    par = Params(T=par.T, n_steps=par.n_steps, delta=par.delta, n_samples=n_samples,
+                 chi_max=chi, cutoff=par.cutoff, n_snapshots=1, seed=par.seed,
+                 sample_offset=sample_offset, precision=1, run_steps=window_steps)
+    tensors, dims = random_mps_tensors(prob.n, chi, seed=mps_seed)
+    return prob, par, (tensors, dims)
