@@ -14,10 +14,12 @@ in mixed-canonical form with an explicit orthogonality centre.
     k_cut   = the smallest k with sum_{j>=k} s_j^2 <= cutoff * sum_j s_j^2;
     k_floor = #{j : s_j > floor_rel * s_0}, which drops singular values that
               are zero to working precision.
-  A cut never splits a group of equal singular values: when
-  s_{k-1} - s_k <= gap_rel * s_0, k drops to the largest k' < k with a clear gap
-  there (the whole tied group is discarded), so that the truncated state is
-  unique. If no such k' >= 1 exists, k stays as it is.
+  A cut never splits a group of (nearly) equal singular values: when
+  s_{k-1} - s_k <= gap_rel * s_0 (default 1e-4), k drops to the largest k' < k
+  with a clear gap there (the whole tied group is discarded). This makes the
+  truncated state unique, and it bounds how far a rounding-level change of
+  theta can move the kept subspace (by about s_k * rounding / gap). If no such
+  k' >= 1 exists, k stays as it is.
 - A single-site gate, and a pi-rotation of a bond term (a product of two
   single-site Paulis), act on the physical index directly. A unitary on one
   site keeps every canonical condition.
@@ -42,7 +44,7 @@ class MPS:
         self.A = [np.asarray(a, dtype=np.complex128) for a in tensors]
         self.c = centre
         self.stats = {"gate_updates": 0, "swap_updates": 0, "qr_moves": 0,
-                      "max_discarded": 0.0, "max_chi": 1}
+                      "max_discarded": 0.0, "max_chi": 1, "min_cut_gap": float("inf")}
 
     @property
     def n(self):
@@ -130,7 +132,7 @@ def keep_count(s: np.ndarray, chi_max: int, cutoff: float, floor_rel: float,
 
 
 def apply_two(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float,
-              floor_rel: float, swap: bool = False, gap_rel: float = 1e-12):
+              floor_rel: float, swap: bool = False, gap_rel: float = 1e-4):
     """Two-site update on bond (i, i+1) with a 4x4 gate g (basis |s_i s_{i+1}>)."""
     move_centre(m, i)
     A, B = m.A[i], m.A[i + 1]
@@ -143,6 +145,10 @@ def apply_two(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float,
     tot = float(np.sum(s.astype(np.float64) ** 2))
     kept = s[:k]
     disc = 0.0 if tot == 0.0 else float(np.sum(s[k:] ** 2)) / tot
+    if k < s.size and s[k] > floor_rel * s[0]:
+        # relative gap at a cut that discards weight: small gaps make the kept
+        # subspace sensitive to rounding-level perturbations
+        m.stats["min_cut_gap"] = min(m.stats["min_cut_gap"], float((s[k - 1] - s[k]) / s[0]))
     kept = kept / np.sqrt(np.sum(kept ** 2))
     m.A[i] = U[:, :k].reshape(chl, 2, k)
     m.A[i + 1] = (kept[:, None] * Vh[:k, :]).reshape(k, 2, chr_)
@@ -177,7 +183,7 @@ class GateCache:
 
 
 def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
-                cutoff: float, floor_rel: float, gap_rel: float = 1e-12):
+                cutoff: float, floor_rel: float, gap_rel: float = 1e-4):
     t = plan.terms[k]
     g = cache.get(k, v)
     if t.pauli == 'Z':
@@ -232,7 +238,7 @@ def expect_z(m: MPS) -> np.ndarray:
 
 
 def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
-               floor_rel: float = 1e-14, gap_rel: float = 1e-12) -> np.ndarray:
+               floor_rel: float = 1e-14, gap_rel: float = 1e-4) -> np.ndarray:
     cache = GateCache(plan)
     out = []
     e = 0
