@@ -46,6 +46,9 @@ extern "C" {
                                           tepai_stats.n_not_converged and its result is still used */
 #define TEPAI_ERR_WORKSPACE_TOO_SMALL 6
 #define TEPAI_ERR_NO_DEVICE         7
+#define TEPAI_ERR_DEVICE_CHECK      8  /* a kernel found a broken invariant (bond dimension out of range,
+                                          non-finite norm); it stopped without touching memory out of
+                                          bounds and the results of that launch are invalid */
 
 /* ---- variants and precisions ----------------------------------------- */
 #define TEPAI_UNBIASED 0  /* TE-PAI with settings A, B, C (App. A.3) */
@@ -103,6 +106,7 @@ typedef struct {
     double alg_flops;              /* 736 chi_l chi chi_r-style algorithmic count, see DESIGN */
     int max_chi;
     int n_not_converged;
+    int device_status[3];          /* first device check failure: (code, detail, CTA); code 0 = none */
 } tepai_stats;
 
 /* Circuit event of one sample: Trotter step j (1-based), term k, setting v

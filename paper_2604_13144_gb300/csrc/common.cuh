@@ -88,10 +88,12 @@ struct KArgs {
   unsigned long long* counter;  // work-queue head
   int x_in_smem;             // the SVD working matrix lives in shared memory
   int smem_x_elems;          // capacity of that buffer (complex elements)
+  int* status;               // [4]: first failure (code, detail, sample, 0); 0 = ok
 };
 
-// Device-visible status word of the ensemble launch.
-enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BAD_DIM = 2 };
+// Device status codes. A CTA that detects a broken invariant records the first
+// failure, touches no more memory for that sample, and leaves the kernel.
+enum : int { ST_OK = 0, ST_BAD_DIM = 1, ST_BAD_RANK = 2, ST_NONFINITE = 3 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t al) { return (x + al - 1) / al * al; }
 

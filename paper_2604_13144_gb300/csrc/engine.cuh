@@ -88,12 +88,25 @@ struct Engine {
   }
 
   __device__ __forceinline__ C* S(int i) const { return site0 + (size_t)i * slot; }
+  // Failure state of this CTA (sm.ibuf[15]); uniform across the CTA after a barrier.
+  __device__ __forceinline__ bool failed() const { return sm.ibuf[15] != 0; }
+  // Record a broken invariant. Called by every thread with uniform arguments.
+  __device__ void fail(int code, int detail) {
+    __syncthreads();
+    if (tid() == 0) {
+      if (atomicCAS(a.status, 0, code) == 0) { a.status[1] = detail; a.status[2] = (int)blockIdx.x; }
+      sm.ibuf[15] = code;
+    }
+    __syncthreads();
+  }
+  __device__ bool dim_ok(int d) const { return d >= 1 && d <= cap; }
   __device__ __forceinline__ int tid() const { return threadIdx.x; }
   __device__ __forceinline__ int nt() const { return blockDim.x; }
 
   // state preparation
   __device__ void init_product();
   __device__ void init_from_tensors();
+  __device__ void normalise_centre();
   // single-site unitary u (2x2 row-major) on site i
   __device__ void apply_1site(int i, const C u[4]);
   // centre moves

@@ -21,11 +21,16 @@ __device__ void Engine<R>::init_product() {
 }
 
 // Copy the shared initial tensors, bring them to right-canonical form with the
-// centre on site 0 (LQ sweep from the right), and normalise the state.
+// centre on site 0 (LQ sweep from the right), and normalise the state. The
+// centre is rescaled to unit norm after every step of the sweep: the norm of an
+// unnormalised input grows geometrically along the chain and would overflow
+// FP32 long before site 0.
 template <typename R>
 __device__ void Engine<R>::init_from_tensors() {
   for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = a.init_dims[i];
   __syncthreads();
+  for (int i = 0; i <= a.n; ++i)
+    if (!dim_ok(sm.dims[i]) || (i == 0 || i == a.n) && sm.dims[i] != 1) { fail(ST_BAD_DIM, 7000 + i); return; }
   size_t off = 0;
   for (int i = 0; i < a.n; ++i) {
     const int cnt = sm.dims[i] * 2 * sm.dims[i + 1];
@@ -36,13 +41,26 @@ __device__ void Engine<R>::init_from_tensors() {
   }
   centre = a.n - 1;
   __syncthreads();
-  move_centre(0);
-  const int cnt = 2 * sm.dims[1];
+  normalise_centre();
+  while (centre > 0 && !failed()) {
+    qr_left();
+    normalise_centre();
+  }
+}
+
+// Rescale the centre tensor (and so the state) to unit norm.
+template <typename R>
+__device__ void Engine<R>::normalise_centre() {
+  if (failed()) return;
+  const int c = centre;
+  const int cnt = sm.dims[c] * 2 * sm.dims[c + 1];
+  C* p = S(c);
   double s2 = 0.0;
-  for (int e = tid(); e < cnt; e += nt()) s2 += (double)abs2(S(0)[e]);
+  for (int e = tid(); e < cnt; e += nt()) s2 += (double)abs2(p[e]);
   s2 = block_sum(s2, sm.red);
+  if (!(s2 > 0.0 && s2 < 1.0e300)) { fail(ST_NONFINITE, 8000 + c); return; }
   const R inv = (R)(1.0 / sqrt(s2));
-  for (int e = tid(); e < cnt; e += nt()) S(0)[e] = scale(S(0)[e], inv);
+  for (int e = tid(); e < cnt; e += nt()) p[e] = scale(p[e], inv);
   __syncthreads();
 }
 
@@ -77,6 +95,7 @@ template <typename R> __device__ __forceinline__ void pauli2(int p, cplx<R> u[4]
 // swapped back; every swap is a truncated two-site update.
 template <typename R>
 __device__ void Engine<R>::apply_event(int k, int v, int& sign_count) {
+  if (failed()) return;
   const TermDev& T = a.terms[k];
   if (tid() == 0) st.events++;
   if (v == 2) sign_count++;
@@ -121,6 +140,7 @@ __device__ void Engine<R>::apply_event(int k, int v, int& sign_count) {
 // <Z_i> for i < c.
 template <typename R>
 __device__ void Engine<R>::measure_z(double* zout) {
+  if (failed()) return;
   const int n = a.n, c = centre;
   C* E = TH;
   C* Tm = TH + (size_t)cap * cap;
@@ -250,7 +270,9 @@ __global__ void __launch_bounds__(512) ensemble_kernel(const __grid_constant__ K
   SmemLayout sm = carve_smem(smem_raw, a, (int)sizeof(cplx<R>));
   char* arena = a.arena + (size_t)blockIdx.x * a.arena_stride;
   Engine<R> eng(a, sm, arena);
-  while (true) {
+  if (threadIdx.x == 0) { sm.ibuf[14] = 0; sm.ibuf[15] = 0; }
+  __syncthreads();
+  while (!eng.failed()) {
     if (threadIdx.x == 0) s_next = (long long)atomicAdd(a.counter, 1ull);
     __syncthreads();
     const long long si = s_next;
@@ -268,6 +290,7 @@ __global__ void __launch_bounds__(512) ensemble_kernel(const __grid_constant__ K
         if (f) eng.apply_event(k, f, sign_count);
       }
       __syncthreads();
+      if (eng.failed()) break;
       while (mi < a.M && a.snaps[mi] == j) {
         eng.measure_z(a.v + ((size_t)si * a.M + mi) * a.n_obs);
         if (threadIdx.x == 0) a.sign[(size_t)si * a.M + mi] = (sign_count & 1) ? -1 : 1;

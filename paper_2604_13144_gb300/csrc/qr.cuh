@@ -96,7 +96,9 @@ __device__ void Engine<R>::householder(C* Y, int m, int nq, C* Q) {
 template <typename R>
 __device__ void Engine<R>::qr_right() {
   const int c = centre;
+  if (c < 0 || c > a.n - 2) { fail(ST_BAD_DIM, 3000 + c); return; }
   const int dl = sm.dims[c], dr = sm.dims[c + 1], d2 = sm.dims[c + 2];
+  if (!dim_ok(dl) || !dim_ok(dr) || !dim_ok(d2)) { fail(ST_BAD_DIM, 4000 + c); return; }
   const int m = 2 * dl, nq = dr, r = min(m, nq);
   C* Y = TH;
   C* Q = XG;
@@ -136,7 +138,9 @@ __device__ void Engine<R>::qr_right() {
 template <typename R>
 __device__ void Engine<R>::qr_left() {
   const int c = centre;
+  if (c < 1 || c > a.n - 1) { fail(ST_BAD_DIM, 5000 + c); return; }
   const int dl = sm.dims[c], dr = sm.dims[c + 1], d0 = sm.dims[c - 1];
+  if (!dim_ok(dl) || !dim_ok(dr) || !dim_ok(d0)) { fail(ST_BAD_DIM, 6000 + c); return; }
   const int m = 2 * dr, nq = dl, r = min(m, nq);
   C* Y = TH;
   C* Q = XG;
@@ -172,8 +176,8 @@ __device__ void Engine<R>::qr_left() {
 
 template <typename R>
 __device__ void Engine<R>::move_centre(int target) {
-  while (centre < target) qr_right();
-  while (centre > target) qr_left();
+  while (centre < target && !failed()) qr_right();
+  while (centre > target && !failed()) qr_left();
 }
 
 }  // namespace tepai

