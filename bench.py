@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="samples per step (0 = 2 per SM)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=64, help="ring size (profiling cases only)")
+    ap.add_argument("--chi", type=int, default=128, help="bond cap (profiling cases only)")
     return ap.parse_args()
 
 
@@ -179,7 +181,7 @@ def run_ours(a):
 
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     batch = a.batch or 2 * sms
-    prob, par, init = W.bench_workload(batch, window_steps=a.window)
+    prob, par, init = W.bench_workload(batch, window_steps=a.window, chi=a.chi, n=a.n)
     stream = torch.cuda.current_stream()
     run = T.DeviceRun(prob, par, init, stream=stream)
     base = 1_000_000 * (rank + 1)
@@ -203,7 +205,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     t0 = time.perf_counter()
-    upd, flops, kms, events = 0.0, 0.0, 0.0, 0.0
+    upd, flops, kms, events, sweeps = 0.0, 0.0, 0.0, 0.0, 0.0
     nconv, maxchi = 0, 0
     for i in range(a.steps):
         ms, st = step(a.warmup + i)
@@ -211,6 +213,7 @@ def run_ours(a):
         upd += st["gate_updates"] + st["swap_updates"]
         flops += st["alg_flops"]
         events += st["events"]
+        sweeps += st["jacobi_sweeps"]
         nconv += st["n_not_converged"]
         maxchi = max(maxchi, st["max_chi"])
     torch.cuda.synchronize()
@@ -235,7 +238,7 @@ def run_ours(a):
     T.tepai_run(ctx, prob, e2e_par, init)           # allocates the context workspace once
     torch.cuda.synchronize()
     e2e_u, t1 = 0.0, time.perf_counter()
-    for i in range(a.e2e_steps):
+    for i in range(max(1, a.e2e_steps)):
         e2e_par = W.Params(**{**par.__dict__, "sample_offset": base + 600_000 + i * batch})
         r = T.tepai_run(ctx, prob, e2e_par, init)
         e2e_u += r["stats"]["gate_updates"] + r["stats"]["swap_updates"]
@@ -255,7 +258,7 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1e3 * elapsed / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "ring64_xxz_chi128_window", "n": n, "chi_max": par.chi_max,
+        "config": {"workload": f"ring{n}_xxz_chi{par.chi_max}_window", "n": n, "chi_max": par.chi_max,
                    "cutoff": par.cutoff, "delta": "pi/1024", "N": par.n_steps, "T": par.T,
                    "window_steps": a.window, "batch": batch, "init": "shared random MPS at chi=128",
                    "precision": "mixed (FP32 tensors/SVD, FP64 bookkeeping)",
@@ -269,6 +272,7 @@ def run_ours(a):
                      "frac": achieved / peak, "traffic": None,
                      "peak_note": "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"},
         "stats": {"events_per_s": events / elapsed, "updates": upd, "alg_flops": flops,
+                  "sweeps_per_svd": sweeps / max(upd, 1.0),
                   "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi},
     }
     if not a.no_cpu_baseline and world == 1:

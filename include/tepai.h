@@ -107,6 +107,9 @@ typedef struct {
     int max_chi;
     int n_not_converged;
     int device_status[3];          /* first device check failure: (code, detail, CTA); code 0 = none */
+    double phase_cycles[8];        /* SM cycles per phase, summed over CTAs: init, sampler,
+                                      single-site gates, theta, Jacobi SVD, truncation and
+                                      write-back, centre moves (QR), measurement */
 } tepai_stats;
 
 /* Circuit event of one sample: Trotter step j (1-based), term k, setting v

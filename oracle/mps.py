@@ -132,8 +132,12 @@ def keep_count(s: np.ndarray, chi_max: int, cutoff: float, floor_rel: float,
 
 
 def apply_two(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float,
-              floor_rel: float, swap: bool = False, gap_rel: float = 1e-4):
-    """Two-site update on bond (i, i+1) with a 4x4 gate g (basis |s_i s_{i+1}>)."""
+              floor_rel: float, swap: bool = False, gap_rel: float = 1e-4,
+              regauge: bool = False):
+    """Two-site update on bond (i, i+1) with a 4x4 gate g (basis |s_i s_{i+1}>).
+    regauge=True moves the centre back to site i afterwards: an exact change of
+    gauge that leaves the state unchanged, used to measure how strongly a run
+    amplifies rounding-level perturbations."""
     move_centre(m, i)
     A, B = m.A[i], m.A[i + 1]
     chl, chr_ = A.shape[0], B.shape[2]
@@ -156,6 +160,8 @@ def apply_two(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float,
     m.stats["swap_updates" if swap else "gate_updates"] += 1
     m.stats["max_discarded"] = max(m.stats["max_discarded"], disc)
     m.stats["max_chi"] = max(m.stats["max_chi"], k)
+    if regauge:
+        move_centre(m, i)
 
 
 def apply_one(m: MPS, i: int, u: np.ndarray):
@@ -183,7 +189,7 @@ class GateCache:
 
 
 def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
-                cutoff: float, floor_rel: float, gap_rel: float = 1e-4):
+                cutoff: float, floor_rel: float, gap_rel: float = 1e-4, regauge: bool = False):
     t = plan.terms[k]
     g = cache.get(k, v)
     if t.pauli == 'Z':
@@ -196,17 +202,19 @@ def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
         return
     n = m.n
     if t.b == t.a + 1:
-        apply_two(m, t.a, g, chi_max, cutoff, floor_rel, gap_rel=gap_rel)
+        apply_two(m, t.a, g, chi_max, cutoff, floor_rel, gap_rel=gap_rel, regauge=regauge)
         return
     # ring bond (n-1, 0): route site n-1 next to site 0 by swaps
     assert t.a == n - 1 and t.b == 0
     for p in range(n - 2, 0, -1):
-        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel)
+        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel,
+                  regauge=regauge)
     # chain bond (0, 1) now holds (site 0, site n-1): reorder the gate basis
     g01 = gates.SWAP @ g @ gates.SWAP
-    apply_two(m, 0, g01, chi_max, cutoff, floor_rel, gap_rel=gap_rel)
+    apply_two(m, 0, g01, chi_max, cutoff, floor_rel, gap_rel=gap_rel, regauge=regauge)
     for p in range(1, n - 1):
-        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel)
+        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel,
+                  regauge=regauge)
 
 
 def expect_z(m: MPS) -> np.ndarray:
@@ -238,7 +246,7 @@ def expect_z(m: MPS) -> np.ndarray:
 
 
 def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
-               floor_rel: float = 1e-14, gap_rel: float = 1e-4) -> np.ndarray:
+               floor_rel: float = 1e-14, gap_rel: float = 1e-4, regauge: bool = False) -> np.ndarray:
     cache = GateCache(plan)
     out = []
     e = 0
@@ -246,7 +254,7 @@ def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
     for js in snap_steps:
         while e < ne and events[e, 0] <= js:
             apply_event(m, plan, cache, int(events[e, 1]), int(events[e, 2]),
-                        chi_max, cutoff, floor_rel, gap_rel)
+                        chi_max, cutoff, floor_rel, gap_rel, regauge)
             e += 1
         out.append(expect_z(m))
     return np.array(out)

@@ -17,7 +17,8 @@ from . import statevector as sv
 
 
 def run(prob, par, init_tensors=None, use_statevector: bool = False,
-        floor_rel: float = 1e-14, gap_rel: float = 1e-4, samples=None):
+        floor_rel: float = 1e-14, gap_rel: float = 1e-4, samples=None,
+        regauge: bool = False):
     """Return dict with v (Ns, M, n_obs), sign (Ns, M), gnorm (M,), mean,
     stderr, partials, events_total and per-sample MPS statistics."""
     plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, par.variant)
@@ -37,7 +38,8 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
         else:
             m = (mps_mod.product_state(prob.init_bits) if init_tensors is None
                  else mps_mod.canonicalize(init_tensors))
-            z = mps_mod.run_events(m, plan, ev, snaps, par.chi_max, par.cutoff, floor_rel, gap_rel)
+            z = mps_mod.run_events(m, plan, ev, snaps, par.chi_max, par.cutoff, floor_rel, gap_rel,
+                                   regauge)
             stats.append(m.stats)
         vs.append(z[:, obs])
         signs.append([sampler.sign_after(ev, j) for j in snaps])

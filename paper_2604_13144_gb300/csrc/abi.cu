@@ -37,8 +37,9 @@ inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 // (the same rule in both precisions, so that both compute the same estimator).
 struct NumCfg { double tol, floor_rel, gap_rel; int max_sweeps; int csize; };
 NumCfg num_cfg(int precision) {
-  if (precision == TEPAI_FP64) return {16 * 1.1102230246251565e-16, 1e-14, 1e-4, 60, 16};
-  return {16 * 5.9604644775390625e-08, 4e-6, 1e-4, 40, 8};
+  // tol is scaled by sqrt(m) in the kernel (m = rows of the orthogonalised matrix)
+  if (precision == TEPAI_FP64) return {2 * 1.1102230246251565e-16, 1e-14, 1e-4, 60, 16};
+  return {2 * 5.9604644775390625e-08, 4e-6, 1e-4, 40, 8};
 }
 
 struct Layout {
@@ -96,9 +97,15 @@ int launch_shape(const HostPlan& hp, const tepai_params* Q, int grid_req, Launch
   const size_t fixed = smem_fixed_bytes(hp.n, hp.L, cap, nc.csize);
   const size_t xbytes = (size_t)4 * cap * cap * nc.csize;
   if (fixed + xbytes <= (size_t)optin) {
+    // the whole SVD working matrix fits in shared memory
     ls.smem = fixed + xbytes; ls.x_in_smem = 1; ls.x_elems = 4 * cap * cap;
   } else {
-    ls.smem = fixed; ls.x_in_smem = 0; ls.x_elems = 0;
+    // two staged column blocks of the working matrix: the largest power-of-two
+    // block width with 2 * bw * 2cap elements within 128 KB
+    int bw = 1;
+    while ((size_t)2 * (2 * bw) * (2 * cap) * nc.csize <= 131072 && 2 * bw < 2 * cap) bw *= 2;
+    ls.x_elems = 2 * bw * 2 * cap;
+    ls.smem = fixed + (size_t)ls.x_elems * nc.csize; ls.x_in_smem = 0;
   }
   if (grid_req > 0) {
     ls.grid = grid_req;
@@ -231,6 +238,7 @@ int stats_impl(void* ws, tepai_stats* out, cudaStream_t st) {
   out->alg_flops = ds.alg_flops;
   out->max_chi = ds.max_chi;
   out->n_not_converged = (int)ds.not_converged;
+  for (int p = 0; p < PH_N; ++p) out->phase_cycles[p] = (double)ds.cycles[p];
   return TEPAI_OK;
 }
 

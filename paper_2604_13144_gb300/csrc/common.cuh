@@ -62,11 +62,15 @@ struct TermDev {
                   // basis |s_a s_b>, (re,im) interleaved; kind 0 uses g[0..7] as 2x2.
 };
 
+// Phases timed with clock64 by thread 0 of every CTA (SM cycles, summed over CTAs).
+enum : int { PH_INIT = 0, PH_SAMPLER, PH_SINGLE, PH_THETA, PH_JACOBI, PH_TRUNC, PH_QR, PH_MEASURE, PH_N };
+
 struct DevStats {
   unsigned long long events, gate_updates, swap_updates, qr_moves, sweeps, not_converged;
   int max_chi, pad;
   double max_discarded;
   double alg_flops;
+  unsigned long long cycles[PH_N];
 };
 
 struct KArgs {

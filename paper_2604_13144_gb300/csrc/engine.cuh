@@ -6,7 +6,8 @@
 //   XG     4*cap*cap complex: SVD working matrix when it does not fit in shared
 //          memory, also the Q factor and temporaries
 // State in shared memory: bond dims, step flags, sort keys, reductions, and
-// the SVD working matrix X when it fits.
+// either the whole SVD working matrix X (when it fits) or two staged column
+// blocks of it.
 // Every member function is called by all threads of the CTA with uniform
 // arguments; they synchronise internally.
 #pragma once
@@ -50,6 +51,24 @@ struct LocalStats {
                      not_converged = 0;
   int max_chi = 1;
   double max_discarded = 0.0, alg_flops = 0.0;
+  unsigned long long cycles[PH_N] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+// Adds the SM cycles of a scope to one phase counter (thread 0 only).
+struct PhaseTimer {
+  LocalStats& st;
+  int ph;
+  long long t0 = 0;
+  __device__ PhaseTimer(LocalStats& s, int p) : st(s), ph(p) {
+#ifdef __CUDA_ARCH__
+    if (threadIdx.x == 0) t0 = clock64();
+#endif
+  }
+  __device__ ~PhaseTimer() {
+#ifdef __CUDA_ARCH__
+    if (threadIdx.x == 0) st.cycles[ph] += (unsigned long long)(clock64() - t0);
+#endif
+  }
 };
 
 // Shared-memory scratch of the engine (fixed part); X follows when it fits.
@@ -117,7 +136,9 @@ struct Engine {
   // two-site update on bond (i, i+1) with gate g (basis |s_i s_{i+1}>)
   __device__ void two_site(int i, const C g[16], bool end_left, bool is_swap);
   __device__ void form_theta(int i, const C g[16], bool end_left, C* X);
-  __device__ int jacobi(C* X, int m, int nc);
+  __device__ int jacobi(C* X, int m, int nc, bool x_in_smem);
+  __device__ void rr_pass(C* X, int m, int nc, R tol, R thr);
+  __device__ void cross_pass(C* XA, int na, C* XB, int nb, int m, R tol, R thr);
   // events
   __device__ void apply_event(int k, int v, int& sign_count);
   // measurement

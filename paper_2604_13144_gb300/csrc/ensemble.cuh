@@ -66,6 +66,7 @@ __device__ void Engine<R>::normalise_centre() {
 
 template <typename R>
 __device__ void Engine<R>::apply_1site(int i, const C u[4]) {
+  PhaseTimer pt(st, PH_SINGLE);
   const int dl = sm.dims[i], dr = sm.dims[i + 1];
   C* p = S(i);
   for (int e = tid(); e < dl * dr; e += nt()) {
@@ -141,6 +142,7 @@ __device__ void Engine<R>::apply_event(int k, int v, int& sign_count) {
 template <typename R>
 __device__ void Engine<R>::measure_z(double* zout) {
   if (failed()) return;
+  PhaseTimer pt(st, PH_MEASURE);
   const int n = a.n, c = centre;
   C* E = TH;
   C* Tm = TH + (size_t)cap * cap;
@@ -264,7 +266,7 @@ __device__ inline SmemLayout carve_smem(unsigned char* base, const KArgs& a, int
 }
 
 template <typename R>
-__global__ void __launch_bounds__(512) ensemble_kernel(const __grid_constant__ KArgs a) {
+__global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_next;
   SmemLayout sm = carve_smem(smem_raw, a, (int)sizeof(cplx<R>));
@@ -279,12 +281,18 @@ __global__ void __launch_bounds__(512) ensemble_kernel(const __grid_constant__ K
     __syncthreads();
     if (si >= a.n_samples) break;
     const unsigned long long s = (unsigned long long)(a.sample_offset + si);
-    if (a.init_tensors) eng.init_from_tensors(); else eng.init_product();
+    {
+      PhaseTimer pt(eng.st, PH_INIT);
+      if (a.init_tensors) eng.init_from_tensors(); else eng.init_product();
+    }
     int sign_count = 0;
     int mi = 0;
     for (long long j = 1; j <= a.run_steps; ++j) {
-      for (int k = threadIdx.x; k < a.L; k += blockDim.x) sm.flags[k] = (unsigned char)draw_gate(a, s, j, k);
-      __syncthreads();
+      {
+        PhaseTimer pt(eng.st, PH_SAMPLER);
+        for (int k = threadIdx.x; k < a.L; k += blockDim.x) sm.flags[k] = (unsigned char)draw_gate(a, s, j, k);
+        __syncthreads();
+      }
       for (int k = 0; k < a.L; ++k) {
         const int f = sm.flags[k];
         if (f) eng.apply_event(k, f, sign_count);
@@ -310,6 +318,7 @@ __global__ void __launch_bounds__(512) ensemble_kernel(const __grid_constant__ K
     atomicMax(reinterpret_cast<unsigned long long*>(&a.stats->max_discarded),
               (unsigned long long)__double_as_longlong(st.max_discarded));
     atomicAdd(&a.stats->alg_flops, st.alg_flops);
+    for (int p = 0; p < PH_N; ++p) atomicAdd(&a.stats->cycles[p], st.cycles[p]);
   }
 }
 

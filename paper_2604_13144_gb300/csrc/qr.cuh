@@ -95,6 +95,7 @@ __device__ void Engine<R>::householder(C* Y, int m, int nq, C* Q) {
 // Centre c -> c+1: A_c (2 d_c x d_{c+1}) = Q R; A_c <- Q, A_{c+1} <- R A_{c+1}.
 template <typename R>
 __device__ void Engine<R>::qr_right() {
+  PhaseTimer pt(st, PH_QR);
   const int c = centre;
   if (c < 0 || c > a.n - 2) { fail(ST_BAD_DIM, 3000 + c); return; }
   const int dl = sm.dims[c], dr = sm.dims[c + 1], d2 = sm.dims[c + 2];
@@ -137,6 +138,7 @@ __device__ void Engine<R>::qr_right() {
 // A_c <- Q'^H (right-orthonormal rows), A_{c-1} <- A_{c-1} R^H.
 template <typename R>
 __device__ void Engine<R>::qr_left() {
+  PhaseTimer pt(st, PH_QR);
   const int c = centre;
   if (c < 1 || c > a.n - 1) { fail(ST_BAD_DIM, 5000 + c); return; }
   const int dl = sm.dims[c], dr = sm.dims[c + 1], d0 = sm.dims[c - 1];

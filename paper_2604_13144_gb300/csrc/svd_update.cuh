@@ -40,69 +40,136 @@ __device__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, C* X)
   __syncthreads();
 }
 
-// Cyclic one-sided Jacobi (Hestenes) on the columns of X (m x nc, column-major),
-// in parallel round-robin order: every round pairs all columns disjointly, one
-// warp per pair; a sweep is nc-1 rounds. A pair (p,q) is rotated when
-// |x_p^H x_q| > tol * |x_p| |x_q|. The complex rotation first removes the phase
+// One Jacobi rotation of the column pair (xp, xq), by one warp: the pair is
+// rotated when |x_p^H x_q| > tol |x_p||x_q| and neither column is below thr
+// (zero to working precision). The complex rotation first removes the phase
 // of x_p^H x_q from x_q, then applies the real Jacobi rotation that zeroes the
-// off-diagonal of the 2x2 Gram matrix. Returns the sweeps run; ibuf[1] = 1
-// when the last sweep rotated nothing (converged).
-// Hestenes, J. SIAM 6 (1958); parallel ordering: Brent & Luk, SIAM J. Sci.
-// Stat. Comput. 6 (1985).
+// off-diagonal of the 2x2 Gram matrix. Returns true (warp-uniform) if rotated.
 template <typename R>
-__device__ int Engine<R>::jacobi(C* X, int m, int nc) {
+__device__ __forceinline__ bool rotate_pair(cplx<R>* xp, cplx<R>* xq, int m, R tol, R thr, int lane) {
+  using C = cplx<R>;
+  R al = 0, be = 0, gr = 0, gi = 0;
+  for (int row = lane; row < m; row += 32) {
+    const C u = xp[row], v = xq[row];
+    al = fma(u.re, u.re, fma(u.im, u.im, al));
+    be = fma(v.re, v.re, fma(v.im, v.im, be));
+    gr = fma(u.re, v.re, fma(u.im, v.im, gr));
+    gi = fma(u.re, v.im, fma(-u.im, v.re, gi));
+  }
+  al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+  if (al < thr || be < thr) return false;
+  const R g = sqrt(gr * gr + gi * gi);
+  if (!(g > tol * sqrt(al * be))) return false;
+  const R zeta = (be - al) / (R(2) * g);
+  const R az = fabs(zeta);
+  R tt = az > R(1) ? R(1) / (az * (R(1) + sqrt(R(1) + R(1) / (az * az))))
+                   : R(1) / (az + sqrt(R(1) + az * az));
+  if (zeta < R(0)) tt = -tt;
+  const R c = rsqrt_<R>(R(1) + tt * tt), s = c * tt;
+  const C e = {gr / g, -gi / g};  // e^{-i phi}
+  for (int row = lane; row < m; row += 32) {
+    const C u = xp[row], v0 = xq[row];
+    const C v = mul(e, v0);
+    xp[row] = C{c * u.re - s * v.re, c * u.im - s * v.im};
+    xq[row] = C{s * u.re + c * v.re, s * u.im + c * v.im};
+  }
+  return true;
+}
+
+// One cyclic pass over all pairs of the nc columns of X (m rows, column-major)
+// in parallel round-robin order (Brent & Luk, SIAM J. Sci. Stat. Comput. 6,
+// 1985): nc-1 rounds of disjoint pairs, one warp per pair. Rotations are
+// counted in ibuf[0].
+template <typename R>
+__device__ void Engine<R>::rr_pass(C* X, int m, int nc, R tol, R thr) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int np = nc + (nc & 1);
-  const R tol = (R)a.tol;
-  int sweep = 0;
-  // Columns below floor_rel/4 of the matrix norm are zero to working precision
+  for (int r = 0; r < np - 1; ++r) {
+    for (int t = w; t < np / 2; t += nw) {
+      int p, q;
+      if (t == 0) { p = np - 1; q = r; }
+      else { p = (r + t) % (np - 1); q = (r - t + np - 1) % (np - 1); }
+      if (p >= nc || q >= nc) continue;
+      if (rotate_pair<R>(X + (size_t)p * m, X + (size_t)q * m, m, tol, thr, lane) && lane == 0)
+        atomicAdd(&sm.ibuf[0], 1);
+    }
+    __syncthreads();
+  }
+}
+
+// All pairs (p in block A, q in block B): round r pairs p with (p + r) mod nmax.
+template <typename R>
+__device__ void Engine<R>::cross_pass(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
+  const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
+  const int nmax = max(na, nb);
+  for (int r = 0; r < nmax; ++r) {
+    for (int p = w; p < nmax; p += nw) {
+      const int q = (p + r) % nmax;
+      if (p >= na || q >= nb) continue;
+      if (rotate_pair<R>(XA + (size_t)p * m, XB + (size_t)q * m, m, tol, thr, lane) && lane == 0)
+        atomicAdd(&sm.ibuf[0], 1);
+    }
+    __syncthreads();
+  }
+}
+
+// Cyclic one-sided Jacobi SVD (Hestenes, J. SIAM 6, 1958) on the columns of X
+// (m x nc, column-major). When X lives in shared memory, each sweep is one
+// round-robin pass. When it does not fit, X stays in global memory and is
+// processed in column blocks of bw: block I is staged in shared memory, its
+// internal pairs are rotated, then every later block J is staged beside it for
+// the cross pairs and written back, and finally I is written back. Every pair
+// is visited once per sweep. Sweeps stop when one rotates nothing; ibuf[1] = 1
+// then, 0 if the sweep cap was hit.
+template <typename R>
+__device__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_smem) {
+  // rotate a pair when |x_p^H x_q| > tol |x_p||x_q|, tol = a.tol * sqrt(m): the
+  // rounding noise of a length-m dot product grows like sqrt(m) eps, so a fixed
+  // tolerance would leave the last sweeps rotating pairs on noise alone
+  const R tol = (R)(a.tol * sqrt((double)m));
+  // columns below floor_rel/4 of the matrix norm are zero to working precision
   // (they will be discarded): they are not rotated, so that the nc - m null
-  // columns of a wide matrix settle instead of shrinking towards underflow.
+  // columns of a wide matrix settle instead of shrinking towards underflow
   double fro = 0.0;
   for (int e = tid(); e < m * nc; e += nt()) fro += (double)abs2(X[e]);
   fro = block_sum(fro, sm.red);
   const R thr = (R)(0.0625 * a.floor_rel * a.floor_rel * fro);
+  int sweep = 0;
   if (tid() == 0) sm.ibuf[1] = 0;
   if (nc < 2) { __syncthreads(); if (tid() == 0) sm.ibuf[1] = 1; __syncthreads(); return 0; }
+  C* xs = reinterpret_cast<C*>(sm.x);
+  int bw = 1;
+  if (!x_in_smem) {
+    while (4 * bw * m <= a.smem_x_elems && 2 * bw < nc) bw *= 2;
+  }
+  const int nbk = x_in_smem ? 1 : (nc + bw - 1) / bw;
   while (sweep < a.max_sweeps) {
     if (tid() == 0) sm.ibuf[0] = 0;
     __syncthreads();
-    for (int r = 0; r < np - 1; ++r) {
-      for (int t = w; t < np / 2; t += nw) {
-        int p, q;
-        if (t == 0) { p = np - 1; q = r; }
-        else { p = (r + t) % (np - 1); q = (r - t + np - 1) % (np - 1); }
-        if (p >= nc || q >= nc) continue;
-        C* xp = X + (size_t)p * m;
-        C* xq = X + (size_t)q * m;
-        R al = 0, be = 0, gr = 0, gi = 0;
-        for (int row = lane; row < m; row += 32) {
-          const C u = xp[row], v = xq[row];
-          al = fma(u.re, u.re, fma(u.im, u.im, al));
-          be = fma(v.re, v.re, fma(v.im, v.im, be));
-          gr = fma(u.re, v.re, fma(u.im, v.im, gr));
-          gi = fma(u.re, v.im, fma(-u.im, v.re, gi));
+    if (x_in_smem) {
+      rr_pass(X, m, nc, tol, thr);
+    } else {
+      C* sa = xs;
+      C* sb = xs + (size_t)bw * m;
+      for (int I = 0; I < nbk; ++I) {
+        const int nI = min(bw, nc - I * bw);
+        const C* gI = X + (size_t)I * bw * m;
+        for (int e = tid(); e < nI * m; e += nt()) sa[e] = gI[e];
+        __syncthreads();
+        rr_pass(sa, m, nI, tol, thr);
+        for (int J = I + 1; J < nbk; ++J) {
+          const int nJ = min(bw, nc - J * bw);
+          C* gJ = X + (size_t)J * bw * m;
+          for (int e = tid(); e < nJ * m; e += nt()) sb[e] = gJ[e];
+          __syncthreads();
+          cross_pass(sa, nI, sb, nJ, m, tol, thr);
+          for (int e = tid(); e < nJ * m; e += nt()) gJ[e] = sb[e];
+          __syncthreads();
         }
-        al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
-        if (al < thr || be < thr) continue;
-        const R g = sqrt(gr * gr + gi * gi);
-        if (!(g > tol * sqrt(al * be))) continue;
-        const R zeta = (be - al) / (R(2) * g);
-        const R az = fabs(zeta);
-        R tt = az > R(1) ? R(1) / (az * (R(1) + sqrt(R(1) + R(1) / (az * az))))
-                         : R(1) / (az + sqrt(R(1) + az * az));
-        if (zeta < R(0)) tt = -tt;
-        const R c = rsqrt_<R>(R(1) + tt * tt), s = c * tt;
-        const C e = {gr / g, -gi / g};  // e^{-i phi}
-        for (int row = lane; row < m; row += 32) {
-          const C u = xp[row], v0 = xq[row];
-          const C v = mul(e, v0);
-          xp[row] = C{c * u.re - s * v.re, c * u.im - s * v.im};
-          xq[row] = C{s * u.re + c * v.re, s * u.im + c * v.im};
-        }
-        if (lane == 0) atomicAdd(&sm.ibuf[0], 1);
+        C* gIw = X + (size_t)I * bw * m;
+        for (int e = tid(); e < nI * m; e += nt()) gIw[e] = sa[e];
+        __syncthreads();
       }
-      __syncthreads();
     }
     ++sweep;
     const int rot = sm.ibuf[0];
@@ -135,10 +202,13 @@ __device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is
   if (!dim_ok(dl) || !dim_ok(dc) || !dim_ok(dr)) { fail(ST_BAD_DIM, 1000 + i); return; }
   const int m = end_left ? 2 * dr : 2 * dl;
   const int nc = end_left ? 2 * dl : 2 * dr;
-  C* X = (a.x_in_smem && m * nc <= a.smem_x_elems) ? reinterpret_cast<C*>(sm.x) : XG;
-  form_theta(i, g, end_left, X);
-  const int sweeps = jacobi(X, m, nc);
+  const bool x_in_smem = m * nc <= a.smem_x_elems;
+  C* X = x_in_smem ? reinterpret_cast<C*>(sm.x) : XG;
+  { PhaseTimer pt(st, PH_THETA); form_theta(i, g, end_left, X); }
+  int sweeps;
+  { PhaseTimer pt(st, PH_JACOBI); sweeps = jacobi(X, m, nc, x_in_smem); }
   const int converged = sm.ibuf[1];
+  PhaseTimer pt_trunc(st, PH_TRUNC);
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   // squared column norms (FP64 accumulation)
   for (int col = w; col < nc; col += nw) {

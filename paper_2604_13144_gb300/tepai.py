@@ -57,11 +57,14 @@ class Stats(C.Structure):
                 ("qr_moves", C.c_double), ("jacobi_sweeps", C.c_double),
                 ("max_discarded_weight", C.c_double), ("alg_flops", C.c_double),
                 ("max_chi", C.c_int), ("n_not_converged", C.c_int),
-                ("device_status", C.c_int * 3)]
+                ("device_status", C.c_int * 3), ("phase_cycles", C.c_double * 8)]
+
+    PHASES = ("init", "sampler", "single_site", "theta", "jacobi", "truncate", "qr", "measure")
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
         d["device_status"] = list(self.device_status)
+        d["phase_cycles"] = dict(zip(self.PHASES, list(self.phase_cycles)))
         return d
 
 

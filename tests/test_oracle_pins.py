@@ -331,3 +331,15 @@ def test_oracle_does_not_import_product_package():
             src = open(os.path.join(here, f)).read()
             assert "paper_2604_13144_gb300" not in src
             assert "import workloads" not in src
+
+
+def test_regauge_leaves_untruncated_results_unchanged():
+    """The gauge change used to measure conditioning is exact: without
+    truncation both gauges give the same <Z_i> to rounding."""
+    prob = W.spin_ring(6, 1.0, seed=6)
+    par = W.Params(T=0.5, n_steps=100, delta=math.pi / 32, n_samples=2, chi_max=8, cutoff=0.0,
+                   n_snapshots=2, seed=2)
+    a = R.run(prob, par)
+    b = R.run(prob, par, regauge=True)
+    assert np.max(np.abs(a["v"] - b["v"])) < 1e-12
+    assert sum(s["qr_moves"] for s in b["stats"]) > sum(s["qr_moves"] for s in a["stats"])

@@ -150,8 +150,10 @@ def config(idx: int) -> tuple[Problem, Params, dict]:
 # --------------------------------------------------------------------------
 
 def bench_workload(n_samples: int, window_steps: int = 2, sample_offset: int = 0,
-                   chi: int = 128, mps_seed: int = 1234):
+                   chi: int = 128, mps_seed: int = 1234, n: int = 64):
     prob, par, extra = config(3)
+    if n != prob.n:
+        prob = spin_ring(n, 1.0, seed=0, Jz=0.5)
     par = Params(T=par.T, n_steps=par.n_steps, delta=par.delta, n_samples=n_samples,
                  chi_max=chi, cutoff=par.cutoff, n_snapshots=1, seed=par.seed,
                  sample_offset=sample_offset, precision=1, run_steps=window_steps)
