@@ -206,6 +206,7 @@ def run_ours(a):
     clk = ClockSampler(local)
     t0 = time.perf_counter()
     upd, flops, kms, events, sweeps = 0.0, 0.0, 0.0, 0.0, 0.0
+    phases = {}
     nconv, maxchi = 0, 0
     for i in range(a.steps):
         ms, st = step(a.warmup + i)
@@ -214,6 +215,8 @@ def run_ours(a):
         flops += st["alg_flops"]
         events += st["events"]
         sweeps += st["jacobi_sweeps"]
+        for k, v in st["phase_cycles"].items():
+            phases[k] = phases.get(k, 0.0) + v
         nconv += st["n_not_converged"]
         maxchi = max(maxchi, st["max_chi"])
     torch.cuda.synchronize()
@@ -273,6 +276,7 @@ def run_ours(a):
                      "peak_note": "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"},
         "stats": {"events_per_s": events / elapsed, "updates": upd, "alg_flops": flops,
                   "sweeps_per_svd": sweeps / max(upd, 1.0),
+                  "phase_share": {k: round(v / max(sum(phases.values()), 1.0), 4) for k, v in phases.items()},
                   "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi},
     }
     if not a.no_cpu_baseline and world == 1:
