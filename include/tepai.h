@@ -172,6 +172,31 @@ int tepai_dev_set_sample_offset(void *d_workspace, long long sample_offset);
 /* Copy the device statistics of the last execute on this workspace. Synchronises `stream`. */
 int tepai_dev_stats(void *d_workspace, tepai_stats *stats, void *stream);
 
+/* ---- entry point without device allocation ------------------------------
+ * The paper has no counterpart: this is a library-usage concern. Some callers
+ * cannot call cudaMalloc, for example code that records a CUDA graph, a host
+ * whose memory pool may not grow, or a plug-in that only receives
+ * pre-allocated buffers. This call runs the same ensemble kernel as
+ * tepai_sample_values, from the product state init_bits, and allocates no device memory. All of its
+ * scratch (tables, counters and one MPS arena per CTA) lives in a 64 MiB
+ * static device array that every GPU loading the library holds until the
+ * process exits. The host-side plan lives in static storage as well.
+ *   d_v    [n_samples][M][n_obs] and d_sign [n_samples][M]: caller-owned device
+ *          buffers (same layout as tepai_sample_values).
+ *   stream cudaStream_t (NULL = legacy default stream). The call waits for
+ *          its work on the stream before it returns.
+ * Sizes: problems with at most 1024 spins; the MPS of one CTA must fit in the
+ * array (n * 2 chi_max^2 + 8 chi_max^2 complex values), otherwise
+ * TEPAI_ERR_WORKSPACE_TOO_SMALL. The number of CTAs is capped by what fits.
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call reuses the same array and leaves its
+ * contents behind; each call clears its own counters. Calls serialise their
+ * host-side part, but two calls whose GPU work overlaps (different streams or
+ * threads) race on the array. */
+int tepai_sample_values_static(const tepai_problem *prob, const tepai_params *par,
+                               double *d_v, signed char *d_sign, void *stream);
+
 const char *tepai_strerror(int code);
 /* Text of the last CUDA error seen by this thread ("" if none). */
 const char *tepai_last_cuda_error(void);

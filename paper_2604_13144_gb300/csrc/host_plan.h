@@ -13,16 +13,49 @@
 
 namespace tepai {
 
-struct HostPlan {
+// Fixed-capacity vector for plans that must not touch the heap.
+template <typename T, size_t N>
+struct FixedVec {
+  T buf[N];
+  size_t n = 0;
+  bool overflow = false;
+  void clear() { n = 0; overflow = false; }
+  void push_back(const T& v) { if (n < N) buf[n++] = v; else overflow = true; }
+  const T* data() const { return buf; }
+  size_t size() const { return n; }
+  const T& operator[](size_t i) const { return buf[i]; }
+};
+
+template <template <typename> class Vec>
+struct PlanT {
   int n = 0, L = 0, M = 0, n_obs = 0, periodic = 0;
   long long N = 0, run_steps = 0;
-  std::vector<TermDev> terms;
-  std::vector<int> snaps;
-  std::vector<double> gnorm;
-  std::vector<int> obs;
-  std::vector<unsigned char> bits;
+  Vec<TermDev> terms;
+  Vec<int> snaps;
+  Vec<double> gnorm;
+  Vec<int> obs;
+  Vec<unsigned char> bits;
   double gnorm_step = 1.0, expected_nu = 0.0;
+  void reset() {
+    n = L = M = n_obs = periodic = 0; N = run_steps = 0; gnorm_step = 1.0; expected_nu = 0.0;
+    terms.clear(); snaps.clear(); gnorm.clear(); obs.clear(); bits.clear();
+  }
+  bool overflowed() const;
 };
+
+template <typename T> using HeapVec = std::vector<T>;
+using HostPlan = PlanT<HeapVec>;
+template <> inline bool HostPlan::overflowed() const { return false; }
+
+// Plan capacity without heap storage: n <= 1024 spins, M <= 4096 snapshots.
+constexpr size_t kFixedMaxN = 1024, kFixedMaxM = 4096;
+template <typename T> struct FixedCap { static constexpr size_t value = 4 * kFixedMaxN; };
+template <> struct FixedCap<double> { static constexpr size_t value = kFixedMaxM; };
+template <typename T> using FixedVecT = FixedVec<T, FixedCap<T>::value>;
+using FixedPlan = PlanT<FixedVecT>;
+template <> inline bool FixedPlan::overflowed() const {
+  return terms.overflow || snaps.overflow || gnorm.overflow || obs.overflow || bits.overflow;
+}
 
 inline bool finite_arr(const double* p, int n) {
   if (!p) return false;
@@ -60,7 +93,8 @@ inline void rotation_gate(int pauli, bool two_site, double phi, double* g) {
     }
 }
 
-inline int build_plan(const tepai_problem* P, const tepai_params* Q, HostPlan& hp) {
+template <class Plan>
+inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   if (!P || !Q) return TEPAI_ERR_INVALID_ARG;
   const int n = P->n;
   if (n < 2) return TEPAI_ERR_INVALID_ARG;
@@ -76,7 +110,7 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, HostPlan& h
   const long long S = Q->run_steps ? Q->run_steps : Q->n_steps;
   if (S < 1 || S > Q->n_steps) return TEPAI_ERR_INVALID_ARG;
   if (Q->n_snapshots < 1 || S % Q->n_snapshots != 0) return TEPAI_ERR_INVALID_ARG;
-  hp = HostPlan();
+  hp.reset();
   hp.n = n; hp.periodic = P->periodic ? 1 : 0; hp.N = Q->n_steps; hp.run_steps = S; hp.M = Q->n_snapshots;
   if (Q->obs_sites) {
     if (Q->n_obs < 1) return TEPAI_ERR_INVALID_ARG;
@@ -91,18 +125,18 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, HostPlan& h
   for (int i = 0; i < n; ++i) hp.bits.push_back(P->init_bits[i] ? 1 : 0);
   // term list: Z_0..Z_{n-1}, then per bond b: XX_b, YY_b, ZZ_b
   struct T0 { int kind, a, b, pauli; double c; };
-  std::vector<T0> tl;
-  for (int i = 0; i < n; ++i) tl.push_back({0, i, i, 2, P->h[i]});
-  for (int b = 0; b < nb; ++b) {
-    const int sa = b, sb = (b + 1) % n;
-    tl.push_back({1, sa, sb, 0, P->Jx[b]});
-    tl.push_back({1, sa, sb, 1, P->Jy[b]});
-    tl.push_back({1, sa, sb, 2, P->Jz[b]});
-  }
-  hp.L = (int)tl.size();
+  hp.L = n + 3 * nb;
   const double delta = Q->delta;
   double sumq = 0.0, gstep = 1.0;
-  for (const T0& t : tl) {
+  for (int k = 0; k < hp.L; ++k) {
+    T0 t;
+    if (k < n) {
+      t = {0, k, k, 2, P->h[k]};
+    } else {
+      const int b = (k - n) / 3, p = (k - n) % 3;
+      const double cc = p == 0 ? P->Jx[b] : (p == 1 ? P->Jy[b] : P->Jz[b]);
+      t = {1, b, (b + 1) % n, p, cc};
+    }
     TermDev td{};
     td.kind = t.kind; td.a = t.a; td.b = t.b; td.pauli = t.pauli;
     const double th = 2.0 * t.c * Q->T / (double)Q->n_steps;
@@ -142,6 +176,7 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, HostPlan& h
     hp.snaps.push_back((int)j);
     hp.gnorm.push_back(std::pow(gstep, (double)j));
   }
+  if (hp.overflowed()) return TEPAI_ERR_INVALID_ARG;
   return TEPAI_OK;
 }
 

@@ -1,0 +1,145 @@
+// tepai_sample_values_static: the ensemble run for callers that cannot
+// allocate device memory. Examples are code that must not call cudaMalloc
+// while a CUDA graph is being built, hosts whose memory pool forbids growth, and
+// plug-ins that only receive pre-allocated buffers. All scratch of this entry point
+// lives in one file-scope device array of fixed size; the caller passes the
+// output buffers.
+#include <cstring>
+#include <mutex>
+
+#include "host_plan.h"
+
+namespace tepai {
+cudaError_t launch_ensemble_f32(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_ensemble_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t occupancy_ensemble_f32(int block, size_t smem, int* ctas_per_sm);
+cudaError_t occupancy_ensemble_f64(int block, size_t smem, int* ctas_per_sm);
+}  // namespace tepai
+
+using namespace tepai;
+
+namespace {
+
+// 64 MiB of scratch, held by every GPU that loads the library until the
+// process exits. In host code `g_static_scratch` is only a host-side stand-in
+// for the symbol: its device address comes from cudaGetSymbolAddress.
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+// Host-side plan of the call in flight, in static storage (no heap); guarded by
+// g_static_mu for the whole call.
+FixedPlan g_static_plan;
+
+inline size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current).
+int static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return TEPAI_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return TEPAI_ERR_INVALID_ARG;
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return TEPAI_ERR_CUDA;
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return TEPAI_OK;
+}
+
+}  // namespace
+
+extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_params* Q, double* d_v,
+                                          signed char* d_sign, void* stream) {
+  if (!d_v || !d_sign) return TEPAI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  FixedPlan& hp = g_static_plan;
+  int rc = build_plan(P, Q, hp);
+  if (rc) return rc;
+  if (Q->n_samples < 1) return TEPAI_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* base_v = nullptr;
+  rc = static_scratch(&base_v);
+  if (rc) return rc;
+  char* base = static_cast<char*>(base_v);
+  const int cap = Q->chi_max;
+  const int csize = Q->precision == TEPAI_FP64 ? 16 : 8;
+  // layout inside the static array: tables, counters, then per-CTA arenas
+  size_t o = 0;
+  const size_t o_terms = o; o = a256(o + sizeof(TermDev) * hp.L);
+  const size_t o_snaps = o; o = a256(o + sizeof(int) * hp.M);
+  const size_t o_obs = o; o = a256(o + sizeof(int) * hp.n_obs);
+  const size_t o_bits = o; o = a256(o + hp.n);
+  const size_t o_stats = o; o = a256(o + sizeof(DevStats));
+  const size_t o_counter = o; o = a256(o + sizeof(unsigned long long));
+  const size_t o_status = o; o = a256(o + 4 * sizeof(int));
+  const size_t o_arena = o;
+  const size_t stride = a256(((size_t)hp.n * 2 * cap * cap + 8 * (size_t)cap * cap) * csize);
+  if (o_arena + stride > kStaticScratchBytes) return TEPAI_ERR_WORKSPACE_TOO_SMALL;
+  // launch shape: the working matrix in shared memory when it fits, else two
+  // staged column blocks (the same rule as the allocating entry points)
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return TEPAI_ERR_CUDA;
+  const int block = cap >= 64 ? 512 : 256;
+  const size_t fixed = smem_fixed_bytes(hp.n, hp.L, cap, csize);
+  size_t smem;
+  int x_elems, x_in_smem;
+  if (fixed + (size_t)4 * cap * cap * csize <= (size_t)optin) {
+    x_elems = 4 * cap * cap; x_in_smem = 1; smem = fixed + (size_t)x_elems * csize;
+  } else {
+    int bw = 1;
+    while ((size_t)2 * (2 * bw) * (2 * cap) * csize <= 131072 && 2 * bw < 2 * cap) bw *= 2;
+    x_elems = 2 * bw * 2 * cap; x_in_smem = 0; smem = fixed + (size_t)x_elems * csize;
+  }
+  int per_sm = 1;
+  if ((Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(block, smem, &per_sm)
+                                  : occupancy_ensemble_f32(block, smem, &per_sm)) != cudaSuccess)
+    return TEPAI_ERR_CUDA;
+  long long grid = (long long)sms * (per_sm < 1 ? 1 : per_sm);
+  const long long fit = (long long)((kStaticScratchBytes - o_arena) / stride);
+  if (grid > fit) grid = fit;
+  if (grid > Q->n_samples) grid = Q->n_samples;
+  // tables (host -> static array) and the counters that must start at zero
+  if (cudaMemcpyAsync(base + o_terms, hp.terms.data(), sizeof(TermDev) * hp.L, cudaMemcpyHostToDevice, st) ||
+      cudaMemcpyAsync(base + o_snaps, hp.snaps.data(), sizeof(int) * hp.M, cudaMemcpyHostToDevice, st) ||
+      cudaMemcpyAsync(base + o_obs, hp.obs.data(), sizeof(int) * hp.n_obs, cudaMemcpyHostToDevice, st) ||
+      cudaMemcpyAsync(base + o_bits, hp.bits.data(), hp.n, cudaMemcpyHostToDevice, st) ||
+      cudaMemsetAsync(base + o_stats, 0, o_arena - o_stats, st))
+    return TEPAI_ERR_CUDA;
+  KArgs a{};
+  a.n = hp.n; a.L = hp.L; a.M = hp.M; a.n_obs = hp.n_obs; a.chi_cap = cap;
+  a.periodic = hp.periodic; a.variant = Q->variant;
+  a.max_sweeps = Q->precision == TEPAI_FP64 ? 60 : 40;
+  a.N = hp.N; a.run_steps = hp.run_steps; a.n_samples = Q->n_samples; a.sample_offset = Q->sample_offset;
+  a.seed = Q->seed; a.cutoff = Q->cutoff;
+  a.floor_rel = Q->precision == TEPAI_FP64 ? 1e-14 : 4e-6;
+  a.tol = Q->precision == TEPAI_FP64 ? 2 * 1.1102230246251565e-16 : 2 * 5.9604644775390625e-08;
+  a.gap_rel = 1e-4;
+  a.terms = reinterpret_cast<const TermDev*>(base + o_terms);
+  a.snaps = reinterpret_cast<const int*>(base + o_snaps);
+  a.obs = reinterpret_cast<const int*>(base + o_obs);
+  a.init_bits = reinterpret_cast<const unsigned char*>(base + o_bits);
+  a.arena = base + o_arena; a.arena_stride = stride;
+  a.v = d_v; a.sign = d_sign;
+  a.stats = reinterpret_cast<DevStats*>(base + o_stats);
+  a.counter = reinterpret_cast<unsigned long long*>(base + o_counter);
+  a.status = reinterpret_cast<int*>(base + o_status);
+  a.x_in_smem = x_in_smem; a.smem_x_elems = x_elems;
+  const cudaError_t le = Q->precision == TEPAI_FP64 ? launch_ensemble_f64(a, (int)grid, block, smem, st)
+                                                    : launch_ensemble_f32(a, (int)grid, block, smem, st);
+  if (le != cudaSuccess) return TEPAI_ERR_CUDA;
+  // the host tables above must outlive their asynchronous copies
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TEPAI_ERR_CUDA;
+  int status = 0;
+  if (cudaMemcpy(&status, base + o_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return TEPAI_ERR_CUDA;
+  return status ? TEPAI_ERR_DEVICE_CHECK : TEPAI_OK;
+}

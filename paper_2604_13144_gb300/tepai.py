@@ -21,7 +21,7 @@ TEPAI_FP64, TEPAI_MIXED = 0, 1
 EXPORTED = ["tepai_create", "tepai_destroy", "tepai_run", "tepai_sample_values",
             "tepai_export_circuit", "tepai_gnorm", "tepai_dev_workspace_size",
             "tepai_dev_prepare", "tepai_dev_execute", "tepai_dev_set_sample_offset",
-            "tepai_dev_stats", "tepai_strerror",
+            "tepai_dev_stats", "tepai_sample_values_static", "tepai_strerror",
             "tepai_last_cuda_error"]
 
 
@@ -91,6 +91,7 @@ def _load():
         "tepai_dev_execute": (i, [vp, vp, vp, vp, vp, vp, vp]),
         "tepai_dev_set_sample_offset": (i, [vp, ll]),
         "tepai_dev_stats": (i, [vp, pS, vp]),
+        "tepai_sample_values_static": (i, [pP, pQ, vp, vp, vp]),
         "tepai_strerror": (C.c_char_p, [i]),
         "tepai_last_cuda_error": (C.c_char_p, []),
     }
@@ -247,3 +248,16 @@ class DeviceRun:
         _check(_lib.tepai_dev_stats(C.c_void_p(self.ws.data_ptr()), C.byref(st),
                                     C.c_void_p(self.stream.cuda_stream)), "tepai_dev_stats")
         return st.as_dict()
+
+
+def tepai_sample_values_static(prob, par, d_v, d_sign, stream=None):
+    """Per-sample values into caller-owned device tensors d_v (float64,
+    [n_samples][M][n_obs]) and d_sign (int8, [n_samples][M]); the library
+    allocates no device memory for this call (its scratch is a fixed static
+    device array)."""
+    m = Marshalled(prob, par)
+    st = stream.cuda_stream if stream is not None else None
+    _check(_lib.tepai_sample_values_static(C.byref(m.prob), C.byref(m.par),
+                                           C.c_void_p(d_v.data_ptr()), C.c_void_p(d_sign.data_ptr()),
+                                           C.c_void_p(st) if st is not None else None),
+           "tepai_sample_values_static")

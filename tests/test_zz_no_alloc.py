@@ -1,0 +1,58 @@
+"""The entry point that allocates no device memory, for callers that cannot
+call cudaMalloc (graph recording, fixed memory pools, plug-ins that only get
+pre-allocated buffers). Its scratch is a fixed static device array. Its results
+must equal those of the allocating entry point within the parity tolerances:
+1e-10 in FP64 and 1e-4 in mixed precision. Two calls run back to back,
+because every call reuses the same array."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2604_13144_gb300 import build
+    build.build()
+    from paper_2604_13144_gb300 import tepai
+    return tepai
+
+
+def _params(**kw):
+    base = dict(T=0.5, n_steps=200, delta=math.pi / 64, n_samples=6, chi_max=8, cutoff=1e-12,
+                n_snapshots=4, seed=3, precision=0)
+    base.update(kw)
+    return W.Params(**base)
+
+
+def test_static_scratch_matches_allocating_entry_point_twice(T):
+    import torch
+    cases = [(W.spin_ring(6, 1.0, seed=1), _params(), 1e-10),
+             (W.spin_ring(8, 1.0, seed=2), _params(chi_max=16, precision=1, seed=4), 1e-4)]
+    ctx = T.tepai_create(0)
+    try:
+        for prob, par, tol in cases:
+            want = T.tepai_sample_values(ctx, prob, par)
+            v = torch.zeros((par.n_samples, par.n_snapshots, prob.n), dtype=torch.float64, device="cuda")
+            sg = torch.zeros((par.n_samples, par.n_snapshots), dtype=torch.int8, device="cuda")
+            T.tepai_sample_values_static(prob, par, v, sg)
+            torch.cuda.synchronize()
+            assert np.max(np.abs(v.cpu().numpy() - want["v"])) <= tol
+            assert np.array_equal(sg.cpu().numpy(), want["sign"])
+    finally:
+        T.tepai_destroy(ctx)
+
+
+def test_static_scratch_rejects_sizes_beyond_its_limit(T):
+    import torch
+    prob = W.spin_ring(64, 1.0, seed=0)
+    par = _params(chi_max=512, n_samples=1, precision=1)      # one MPS arena exceeds 64 MiB
+    v = torch.zeros((1, 4, 64), dtype=torch.float64, device="cuda")
+    sg = torch.zeros((1, 4), dtype=torch.int8, device="cuda")
+    with pytest.raises(T.TepaiError) as e:
+        T.tepai_sample_values_static(prob, par, v, sg)
+    assert e.value.code == 6
