@@ -1,5 +1,6 @@
 // C-ABI of libtepai.so: workspace layout, launches and host-buffer wrappers.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -40,6 +41,13 @@ NumCfg num_cfg(int precision) {
   // tol is scaled by sqrt(m) in the kernel (m = rows of the orthogonalised matrix)
   if (precision == TEPAI_FP64) return {2 * 1.1102230246251565e-16, 1e-14, 1e-4, 60, 16};
   return {2 * 5.9604644775390625e-08, 4e-6, 1e-4, 40, 8};
+}
+
+// QR preconditioning of the Jacobi SVD: on unless TEPAI_JACOBI_PRECONDITION=0
+// (kept switchable for A/B timing of the two SVD variants).
+int jacobi_precondition() {
+  const char* e = std::getenv("TEPAI_JACOBI_PRECONDITION");
+  return (e && e[0] == '0') ? 0 : 1;
 }
 
 struct Layout {
@@ -180,6 +188,7 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   a.counter = reinterpret_cast<unsigned long long*>(base + L.counter);
   a.status = reinterpret_cast<int*>(base + L.status);
   a.x_in_smem = ls.x_in_smem; a.smem_x_elems = ls.x_elems;
+  a.precondition = jacobi_precondition();
   pr.precision = Q->precision; pr.grid = ls.grid; pr.block = ls.block; pr.smem = ls.smem;
   pr.n_samples = Q->n_samples; pr.M = hp.M; pr.n_obs = hp.n_obs;
   pr.gnorm = reinterpret_cast<double*>(base + L.gnorm);

@@ -93,6 +93,7 @@ struct KArgs {
   int x_in_smem;             // the SVD working matrix lives in shared memory
   int smem_x_elems;          // capacity of that buffer (complex elements)
   int* status;               // [4]: first failure (code, detail, sample, 0); 0 = ok
+  int precondition;          // 1 = QR-preconditioned Jacobi where the shapes allow it
 };
 
 // Device status codes. A CTA that detects a broken invariant records the first

@@ -132,10 +132,10 @@ struct Engine {
   __device__ void move_centre(int target);
   __device__ void qr_right();
   __device__ void qr_left();
-  __device__ void householder(C* Y, int m, int nq, C* Q);
+  __device__ void householder(C* Y, int m, int nq, C* Q, double tiny2);
   // two-site update on bond (i, i+1) with gate g (basis |s_i s_{i+1}>)
   __device__ void two_site(int i, const C g[16], bool end_left, bool is_swap);
-  __device__ void form_theta(int i, const C g[16], bool end_left, C* X);
+  __device__ void form_theta(int i, const C g[16], bool end_left, bool zh, C* X);
   __device__ int jacobi(C* X, int m, int nc, bool x_in_smem);
   __device__ void rr_pass(C* X, int m, int nc, R tol, R thr);
   __device__ void cross_pass(C* XA, int na, C* XB, int nb, int m, R tol, R thr);

@@ -9,9 +9,13 @@ namespace tepai {
 // Reflector j is H_j = I - tau_j v_j v_j^H, v_j = (vhead_j, Y[j+1.., j]); it maps
 // the column onto alpha_j e_j with alpha_j = -e^{i arg x_0} |x|. On return the
 // strict upper triangle of R is in Y, its diagonal in alpha[], and Q (m x r,
-// column-major) is formed explicitly by backward accumulation.
+// column-major) is formed explicitly by backward accumulation unless Q is null.
+// A reflector is skipped (tau = 0) when the remaining column has |x|^2 <= tiny2,
+// or when tau = 1/(|x|(|x|+|x_0|)) is not finite: an evolved state carries
+// amplitudes like sin(Delta/2)^k whose squares underflow FP32, and the scale
+// would overflow.
 template <typename R>
-__device__ void Engine<R>::householder(C* Y, int m, int nq, C* Q) {
+__device__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, double tiny2) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int r = min(m, nq);
   C* vhead = reinterpret_cast<C*>(sm.hh);
@@ -27,13 +31,14 @@ __device__ void Engine<R>::householder(C* Y, int m, int nq, C* Q) {
         const C x0 = y[j];
         const R ax0 = sqrt(abs2(x0));
         const R nrm = sqrt(nr2);
-        if (!(nrm > R(0))) {
-          vhead[j] = C{1, 0}; tau[j] = C{0, 0}; alpha[j] = C{0, 0};
+        const R tj = R(1) / (nrm * (nrm + ax0));
+        if (!((double)nr2 > tiny2) || !(nrm > R(0)) || !isfinite(tj)) {
+          vhead[j] = C{1, 0}; tau[j] = C{0, 0}; alpha[j] = x0;
         } else {
           const C ph = ax0 > R(0) ? C{x0.re / ax0, x0.im / ax0} : C{1, 0};
           alpha[j] = C{-ph.re * nrm, -ph.im * nrm};
           vhead[j] = C{ph.re * (ax0 + nrm), ph.im * (ax0 + nrm)};
-          tau[j] = C{R(1) / (nrm * (nrm + ax0)), 0};
+          tau[j] = C{tj, 0};
         }
       }
     }
@@ -61,6 +66,7 @@ __device__ void Engine<R>::householder(C* Y, int m, int nq, C* Q) {
     }
     __syncthreads();
   }
+  if (Q == nullptr) return;
   for (int e = tid(); e < m * r; e += nt()) {
     const int col = e / m, row = e - col * m;
     Q[e] = C{row == col ? R(1) : R(0), 0};
@@ -109,7 +115,7 @@ __device__ void Engine<R>::qr_right() {
     Y[(size_t)b * m + row] = Ac[e];
   }
   __syncthreads();
-  householder(Y, m, nq, Q);
+  householder(Y, m, nq, Q, 0.0);
   C* Acw = S(c);
   for (int e = tid(); e < m * r; e += nt()) {
     const int row = e / r, col = e - row * r;
@@ -149,7 +155,7 @@ __device__ void Engine<R>::qr_left() {
   const C* Ac = S(c);
   for (int e = tid(); e < m * nq; e += nt()) { const C v = Ac[e]; Y[e] = C{v.re, -v.im}; }
   __syncthreads();
-  householder(Y, m, nq, Q);
+  householder(Y, m, nq, Q, 0.0);
   C* Acw = S(c);
   for (int e = tid(); e < r * m; e += nt()) { const C v = Q[e]; Acw[e] = C{v.re, -v.im}; }
   __syncthreads();

@@ -7,11 +7,13 @@
 namespace tepai {
 
 // theta'[(a,s),(t,b)] = sum_{s't'} g[st][s't'] sum_c A_i[a,s',c] A_{i+1}[c,t',b].
-// TH receives theta' row-major (2dl x 2dr). X receives the matrix whose columns
-// the SVD orthogonalises, column-major: theta' itself when the centre ends on
-// the right site, theta'^T when it ends on the left site.
+// TH receives theta' row-major (2dl x 2dr). X receives, column-major, the
+// matrix Z whose left singular vectors become the orthonormal site: Z = theta'
+// when the centre ends on the right site, Z = theta'^T when it ends on the
+// left. With zh set, X receives Z^H instead (the input of the preconditioning
+// QR): theta'^H (ld 2dr) or conj(theta') (ld 2dl).
 template <typename R>
-__device__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, C* X) {
+__device__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, bool zh, C* X) {
   const int dl = sm.dims[i], dc = sm.dims[i + 1], dr = sm.dims[i + 2];
   const C* A = S(i);
   const C* B = S(i + 1);
@@ -33,8 +35,14 @@ __device__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, C* X)
       for (int q = 0; q < 4; ++q) fma_c(o, g[s4 * 4 + q], t[q]);
       const int row = aa * 2 + (s4 >> 1), col = (s4 & 1) * dr + bb;
       TH[(size_t)row * ncol + col] = o;
-      if (end_left) X[(size_t)row * ncol + col] = o;
-      else X[(size_t)col * m + row] = o;
+      if (!zh) {
+        if (end_left) X[(size_t)row * ncol + col] = o;
+        else X[(size_t)col * m + row] = o;
+      } else {
+        const C oc = {o.re, -o.im};
+        if (end_left) X[(size_t)col * m + row] = oc;
+        else X[(size_t)row * ncol + col] = oc;
+      }
     }
   }
   __syncthreads();
@@ -44,17 +52,23 @@ __device__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, C* X)
 // rotated when |x_p^H x_q| > tol |x_p||x_q| and neither column is below thr
 // (zero to working precision). The complex rotation first removes the phase
 // of x_p^H x_q from x_q, then applies the real Jacobi rotation that zeroes the
-// off-diagonal of the 2x2 Gram matrix. Returns true (warp-uniform) if rotated.
-template <typename R>
+// off-diagonal of the 2x2 Gram matrix. Each lane keeps its RPL rows of both
+// columns in registers between the inner products and the rotation
+// (m <= 32 * RPL). Returns true (warp-uniform) if rotated.
+template <typename R, int RPL>
 __device__ __forceinline__ bool rotate_pair(cplx<R>* xp, cplx<R>* xq, int m, R tol, R thr, int lane) {
   using C = cplx<R>;
+  C u[RPL], v[RPL];
   R al = 0, be = 0, gr = 0, gi = 0;
-  for (int row = lane; row < m; row += 32) {
-    const C u = xp[row], v = xq[row];
-    al = fma(u.re, u.re, fma(u.im, u.im, al));
-    be = fma(v.re, v.re, fma(v.im, v.im, be));
-    gr = fma(u.re, v.re, fma(u.im, v.im, gr));
-    gi = fma(u.re, v.im, fma(-u.im, v.re, gi));
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int row = lane + 32 * t;
+    if (row < m) { u[t] = xp[row]; v[t] = xq[row]; }
+    else { u[t] = C{0, 0}; v[t] = C{0, 0}; }
+    al = fma(u[t].re, u[t].re, fma(u[t].im, u[t].im, al));
+    be = fma(v[t].re, v[t].re, fma(v[t].im, v[t].im, be));
+    gr = fma(u[t].re, v[t].re, fma(u[t].im, v[t].im, gr));
+    gi = fma(u[t].re, v[t].im, fma(-u[t].im, v[t].re, gi));
   }
   al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
   if (al < thr || be < thr) return false;
@@ -66,14 +80,25 @@ __device__ __forceinline__ bool rotate_pair(cplx<R>* xp, cplx<R>* xq, int m, R t
                    : R(1) / (az + sqrt(R(1) + az * az));
   if (zeta < R(0)) tt = -tt;
   const R c = rsqrt_<R>(R(1) + tt * tt), s = c * tt;
-  const C e = {gr / g, -gi / g};  // e^{-i phi}
-  for (int row = lane; row < m; row += 32) {
-    const C u = xp[row], v0 = xq[row];
-    const C v = mul(e, v0);
-    xp[row] = C{c * u.re - s * v.re, c * u.im - s * v.im};
-    xq[row] = C{s * u.re + c * v.re, s * u.im + c * v.im};
+  const R er = gr / g, ei = -gi / g;  // e^{-i phi}
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int row = lane + 32 * t;
+    const C w = {er * v[t].re - ei * v[t].im, er * v[t].im + ei * v[t].re};
+    if (row < m) {
+      xp[row] = C{c * u[t].re - s * w.re, c * u[t].im - s * w.im};
+      xq[row] = C{s * u[t].re + c * w.re, s * u[t].im + c * w.im};
+    }
   }
   return true;
+}
+
+template <typename R>
+__device__ __forceinline__ bool rotate_pair_m(cplx<R>* xp, cplx<R>* xq, int m, R tol, R thr, int lane) {
+  if (m <= 64) return rotate_pair<R, 2>(xp, xq, m, tol, thr, lane);
+  if (m <= 128) return rotate_pair<R, 4>(xp, xq, m, tol, thr, lane);
+  if (m <= 256) return rotate_pair<R, 8>(xp, xq, m, tol, thr, lane);
+  return rotate_pair<R, 16>(xp, xq, m, tol, thr, lane);
 }
 
 // One cyclic pass over all pairs of the nc columns of X (m rows, column-major)
@@ -90,7 +115,7 @@ __device__ void Engine<R>::rr_pass(C* X, int m, int nc, R tol, R thr) {
       if (t == 0) { p = np - 1; q = r; }
       else { p = (r + t) % (np - 1); q = (r - t + np - 1) % (np - 1); }
       if (p >= nc || q >= nc) continue;
-      if (rotate_pair<R>(X + (size_t)p * m, X + (size_t)q * m, m, tol, thr, lane) && lane == 0)
+      if (rotate_pair_m<R>(X + (size_t)p * m, X + (size_t)q * m, m, tol, thr, lane) && lane == 0)
         atomicAdd(&sm.ibuf[0], 1);
     }
     __syncthreads();
@@ -106,7 +131,7 @@ __device__ void Engine<R>::cross_pass(C* XA, int na, C* XB, int nb, int m, R tol
     for (int p = w; p < nmax; p += nw) {
       const int q = (p + r) % nmax;
       if (p >= na || q >= nb) continue;
-      if (rotate_pair<R>(XA + (size_t)p * m, XB + (size_t)q * m, m, tol, thr, lane) && lane == 0)
+      if (rotate_pair_m<R>(XA + (size_t)p * m, XB + (size_t)q * m, m, tol, thr, lane) && lane == 0)
         atomicAdd(&sm.ibuf[0], 1);
     }
     __syncthreads();
@@ -202,16 +227,69 @@ __device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is
   if (!dim_ok(dl) || !dim_ok(dc) || !dim_ok(dr)) { fail(ST_BAD_DIM, 1000 + i); return; }
   const int m = end_left ? 2 * dr : 2 * dl;
   const int nc = end_left ? 2 * dl : 2 * dr;
-  const bool x_in_smem = m * nc <= a.smem_x_elems;
-  C* X = x_in_smem ? reinterpret_cast<C*>(sm.x) : XG;
-  { PhaseTimer pt(st, PH_THETA); form_theta(i, g, end_left, X); }
+  // Preconditioned Jacobi (Drmac & Veselic, SIAM J. Matrix Anal. Appl. 29,
+  // 2008): Z^H = Q R by Householder (Q not formed), then one-sided Jacobi on the
+  // columns of X = R^H. Z = R^H Q^H, so the normalised columns of X J are the
+  // left singular vectors of Z while needing far fewer sweeps than Z itself.
+  // X = R^H lives in shared memory when it fits, or replaces R in place when
+  // Z is square; other shapes run plain Jacobi on Z.
+  const int r = min(m, nc);
+  const bool y_smem = (m == nc) && (m * nc <= a.smem_x_elems);
+  const bool x_smem = y_smem || (m * r <= a.smem_x_elems);
+  const bool pre = a.precondition && (x_smem || m == nc);
+  C* xs = reinterpret_cast<C*>(sm.x);
+  C* X;
+  int ncx;
+  if (pre) {
+    C* Y = y_smem ? xs : XG;
+    { PhaseTimer pt(st, PH_THETA); form_theta(i, g, end_left, true, Y); }
+    {
+      PhaseTimer pt(st, PH_QR);
+      double fro = 0.0;
+      for (int e = tid(); e < m * nc; e += nt()) fro += (double)abs2(Y[e]);
+      fro = block_sum(fro, sm.red);
+      // skip only reflectors whose 1/|x|^2 scale would overflow; smaller
+      // columns are still rotated exactly (dropping them would lose their weight)
+      householder(Y, nc, m, nullptr, (sizeof(R) == 4 ? 1e-30 : 1e-280) * fro);
+      const C* alpha = reinterpret_cast<const C*>(sm.hh) + 4 * cap;
+      X = x_smem ? xs : XG;
+      if (X == Y) {
+        // square: move the upper triangle of R to X = R^H in place
+        for (int e = tid(); e < m * m; e += nt()) {
+          const int ca = e / m, rj = e - ca * m;
+          if (ca > rj) {
+            const C u = Y[(size_t)ca * m + rj];
+            X[(size_t)rj * m + ca] = C{u.re, -u.im};
+            X[(size_t)ca * m + rj] = C{0, 0};
+          } else if (ca == rj) {
+            X[(size_t)rj * m + rj] = C{alpha[rj].re, -alpha[rj].im};
+          }
+        }
+      } else {
+        for (int e = tid(); e < m * r; e += nt()) {
+          const int j = e / m, aa = e - j * m;
+          C v = {0, 0};
+          if (aa > j) { const C u = Y[(size_t)aa * nc + j]; v = C{u.re, -u.im}; }
+          else if (aa == j) v = C{alpha[j].re, -alpha[j].im};
+          X[e] = v;
+        }
+      }
+      __syncthreads();
+    }
+    ncx = r;
+  } else {
+    const bool x_in = m * nc <= a.smem_x_elems;
+    X = x_in ? xs : XG;
+    { PhaseTimer pt(st, PH_THETA); form_theta(i, g, end_left, false, X); }
+    ncx = nc;
+  }
   int sweeps;
-  { PhaseTimer pt(st, PH_JACOBI); sweeps = jacobi(X, m, nc, x_in_smem); }
+  { PhaseTimer pt(st, PH_JACOBI); sweeps = jacobi(X, m, ncx, X == xs); }
   const int converged = sm.ibuf[1];
   PhaseTimer pt_trunc(st, PH_TRUNC);
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   // squared column norms (FP64 accumulation)
-  for (int col = w; col < nc; col += nw) {
+  for (int col = w; col < ncx; col += nw) {
     const C* x = X + (size_t)col * m;
     double s2 = 0.0;
     for (int row = lane; row < m; row += 32) s2 += (double)abs2(x[row]);
@@ -225,12 +303,12 @@ __device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is
   const int bad_norm = sm.ibuf[14];
   __syncthreads();
   if (bad_norm) { if (tid() == 0) sm.ibuf[14] = 0; fail(ST_NONFINITE, 2000 + i); return; }
-  for (int j = tid(); j < nc; j += nt()) sm.perm[j] = -1;
+  for (int j = tid(); j < ncx; j += nt()) sm.perm[j] = -1;
   __syncthreads();
-  for (int j = tid(); j < nc; j += nt()) {
+  for (int j = tid(); j < ncx; j += nt()) {
     const double wj = sm.wn[j];
     int rank = 0;
-    for (int q = 0; q < nc; ++q) {
+    for (int q = 0; q < ncx; ++q) {
       const double wq = sm.wn[q];
       rank += (wq > wj) || (wq == wj && q < j);
     }
@@ -239,25 +317,25 @@ __device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is
   __syncthreads();
   // the ranks of finite keys form a permutation; check before indexing with it
   int bad_perm = 0;
-  for (int j = tid(); j < nc; j += nt()) bad_perm |= (sm.perm[j] < 0 || sm.perm[j] >= nc);
+  for (int j = tid(); j < ncx; j += nt()) bad_perm |= (sm.perm[j] < 0 || sm.perm[j] >= ncx);
   if (__syncthreads_or(bad_perm)) { fail(ST_BAD_RANK, 9000 + i); return; }
   if (tid() == 0) {
     double tot = 0.0;
-    for (int j = nc - 1; j >= 0; --j) tot += sm.wn[sm.perm[j]];
+    for (int j = ncx - 1; j >= 0; --j) tot += sm.wn[sm.perm[j]];
     const double thr = a.cutoff * tot;
-    int kcut = nc;
+    int kcut = ncx;
     double acc = 0.0;
-    for (int j = nc - 1; j >= 1; --j) {
+    for (int j = ncx - 1; j >= 1; --j) {
       acc += sm.wn[sm.perm[j]];
       if (acc <= thr) kcut = j; else break;
     }
     const double s0 = sqrt(sm.wn[sm.perm[0]]);
     int kfloor = 0;
-    while (kfloor < nc && sqrt(sm.wn[sm.perm[kfloor]]) > a.floor_rel * s0) ++kfloor;
-    int k = min(min(cap, kfloor), min(kcut, min(m, nc)));
+    while (kfloor < ncx && sqrt(sm.wn[sm.perm[kfloor]]) > a.floor_rel * s0) ++kfloor;
+    int k = min(min(cap, kfloor), min(kcut, min(m, ncx)));
     if (k < 1) k = 1;
     // never split a group of equal singular values: drop the whole group
-    if (k < nc && sqrt(sm.wn[sm.perm[k]]) > a.floor_rel * s0) {
+    if (k < ncx && sqrt(sm.wn[sm.perm[k]]) > a.floor_rel * s0) {
       int kk = k;
       while (kk >= 1 && sqrt(sm.wn[sm.perm[kk - 1]]) - sqrt(sm.wn[sm.perm[kk]]) <= a.gap_rel * s0) --kk;
       if (kk >= 1) k = kk;
