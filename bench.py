@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="samples per step (0 = 2 per SM)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tts", action="store_true", help="skip the config-1 time-to-<Z> comparison")
     ap.add_argument("--n", type=int, default=64, help="ring size (profiling cases only)")
     ap.add_argument("--chi", type=int, default=128, help="bond cap (profiling cases only)")
     return ap.parse_args()
@@ -159,6 +160,40 @@ def run_reference(a):
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------- time to <Z>, config 1
+def tts_config1(T, W, torch, local, subset=16):
+    """Time-to-<Z_0> on configuration 1 (ring of 8, 1000 samples, N = 2000):
+    mixed precision with batched persistent CTAs, against the plain FP64 form
+    with one sample per launch (timed on `subset` samples, scaled to 1000).
+    The error is max |mean_mixed - mean_fp64| on the same seeded circuits. The
+    FP64 path equals the oracle to 1e-10 in the parity tests."""
+    prob, par, _ = W.config(1)
+    ctx = T.tepai_create(local)
+    try:
+        mixed = W.Params(**{**par.__dict__, "precision": 1})
+        T.tepai_run(ctx, prob, W.Params(**{**mixed.__dict__, "n_samples": 8}))   # context set-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rm = T.tepai_run(ctx, prob, mixed)
+        t_mixed = time.perf_counter() - t
+        t = time.perf_counter()
+        rf = T.tepai_run(ctx, prob, par)
+        t_fp64_batched = time.perf_counter() - t
+        t = time.perf_counter()
+        for s in range(subset):
+            T.tepai_run(ctx, prob, W.Params(**{**par.__dict__, "n_samples": 1, "sample_offset": s}))
+        t_one = (time.perf_counter() - t) / subset * par.n_samples
+    finally:
+        T.tepai_destroy(ctx)
+    err = float(abs(rm["mean"] - rf["mean"]).max())
+    return {"config": "ring8_heisenberg_T1 (N=2000, 1000 samples, chi_max=16, <Z_0> at 10 times)",
+            "mixed_batched_s": t_mixed, "fp64_batched_s": t_fp64_batched,
+            "fp64_one_sample_per_launch_s": t_one, "one_per_launch_subset": subset,
+            "speedup_vs_fp64_one_per_launch": t_one / t_mixed,
+            "max_abs_err_mixed_vs_fp64": err,
+            "stderr_fp64": float(rf["stderr"].max())}
 
 
 # ---------------------------------------------------------------- our arm
@@ -279,6 +314,8 @@ def run_ours(a):
                   "phase_share": {k: round(v / max(sum(phases.values()), 1.0), 4) for k, v in phases.items()},
                   "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi},
     }
+    if not a.no_tts and world == 1:
+        line["tts_config1"] = tts_config1(T, W, torch, local)
     if not a.no_cpu_baseline and world == 1:
         procs = max(1, min(cpu_cores(), 16))
         u, t = oracle_sample(1, [base + 900_000 + i for i in range(procs)], procs)
