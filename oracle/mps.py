@@ -1,7 +1,11 @@
 """Plain FP64 matrix-product-state simulator of one TE-PAI circuit (Sec. II.A).
 
-Open chain in natural site order. Site tensors are A_i[chi_{i-1}][2][chi_i]
-in mixed-canonical form with an explicit orthogonality centre.
+Site tensors are A_p[chi_{p-1}][2][chi_p] over chain positions p, in
+mixed-canonical form with an explicit orthogonality centre. An open chain uses
+the natural site order. A ring (periodic boundary of Sec. III, Eq. spinRing)
+uses the folded order 0, n-1, 1, n-2, 2, ..., so that every ring bond joins
+chain positions at distance 1 or 2 and every cut crosses two ring bonds, as
+in the natural order.
 
 - A two-site gate on bond (i, i+1) moves the centre to site i (Householder
   QR / LQ through numpy.linalg.qr) and forms theta = A_i A_{i+1}. It applies
@@ -23,9 +27,9 @@ in mixed-canonical form with an explicit orthogonality centre.
 - A single-site gate, and a pi-rotation of a bond term (a product of two
   single-site Paulis), act on the physical index directly. A unitary on one
   site keeps every canonical condition.
-- A gate on the ring bond (n-1, 0) is routed by swaps: site n-1 is swapped
-  left to position 1, the gate acts on chain bond (0, 1), and the site is
-  swapped back. Every swap is a two-site update with truncation.
+- A gate on sites two chain positions apart (p, p+2) swaps positions p+1 and
+  p+2, acts on chain bond (p, p+1), and swaps back. Every swap is a two-site
+  update with truncation.
 - <Z_i> is contracted with left and right environments. This makes no
   canonical-form assumption.
 """
@@ -39,10 +43,29 @@ from .sampler import EV_B, EV_C, EV_T
 ZDIAG = np.array([1.0, -1.0])
 
 
+def chain_order(n: int, periodic: bool) -> list:
+    """Ring site held by each chain position: natural for an open chain;
+    0, n-1, 1, n-2, 2, ... for a ring."""
+    if not periodic:
+        return list(range(n))
+    out, lo, hi = [], 0, n - 1
+    while lo <= hi:
+        out.append(lo)
+        lo += 1
+        if lo <= hi:
+            out.append(hi)
+            hi -= 1
+    return out
+
+
 class MPS:
-    def __init__(self, tensors, centre: int):
+    def __init__(self, tensors, centre: int, periodic: bool = False):
         self.A = [np.asarray(a, dtype=np.complex128) for a in tensors]
         self.c = centre
+        self.order = chain_order(len(self.A), periodic)
+        self.pos = [0] * len(self.A)
+        for p, site in enumerate(self.order):
+            self.pos[site] = p
         self.stats = {"gate_updates": 0, "swap_updates": 0, "qr_moves": 0,
                       "max_discarded": 0.0, "max_chi": 1, "min_cut_gap": float("inf")}
 
@@ -54,13 +77,15 @@ class MPS:
         return [1] + [a.shape[2] for a in self.A[:-1]] + [1]
 
 
-def product_state(bits) -> MPS:
+def product_state(bits, periodic: bool = False) -> MPS:
+    """|b_0 b_1 ...> over ring sites, stored in chain order."""
+    order = chain_order(len(bits), periodic)
     ts = []
-    for b in bits:
+    for site in order:
         a = np.zeros((1, 2, 1), dtype=np.complex128)
-        a[0, int(b), 0] = 1.0
+        a[0, int(bits[site]), 0] = 1.0
         ts.append(a)
-    return MPS(ts, 0)
+    return MPS(ts, 0, periodic)
 
 
 def _move_right(m: MPS):
@@ -93,10 +118,10 @@ def move_centre(m: MPS, target: int):
         _move_left(m)
 
 
-def canonicalize(tensors) -> MPS:
-    """Bring arbitrary site tensors to right-canonical form with the centre
-    on site 0, then normalise the state."""
-    m = MPS(tensors, len(tensors) - 1)
+def canonicalize(tensors, periodic: bool = False) -> MPS:
+    """Bring arbitrary site tensors (given in chain order) to right-canonical
+    form with the centre on chain position 0, then normalise the state."""
+    m = MPS(tensors, len(tensors) - 1, periodic)
     move_centre(m, 0)
     m.A[0] = m.A[0] / np.linalg.norm(m.A[0])
     m.stats["qr_moves"] = 0
@@ -193,32 +218,33 @@ def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
     t = plan.terms[k]
     g = cache.get(k, v)
     if t.pauli == 'Z':
-        apply_one(m, t.a, g)
+        apply_one(m, m.pos[t.a], g)
         return
+    pa, pb = m.pos[t.a], m.pos[t.b]
     if v == EV_C:
         # R_k(pi) = -i P (x) P: one Pauli on each site, global phase dropped
-        apply_one(m, t.a, g)
-        apply_one(m, t.b, g)
+        apply_one(m, pa, g)
+        apply_one(m, pb, g)
         return
-    n = m.n
-    if t.b == t.a + 1:
-        apply_two(m, t.a, g, chi_max, cutoff, floor_rel, gap_rel=gap_rel, regauge=regauge)
+    # gate basis |s_lo s_hi> over the lower and upper chain position
+    lo, hi = (pa, pb) if pa < pb else (pb, pa)
+    if pa > pb:
+        g = gates.SWAP @ g @ gates.SWAP
+    if hi - lo == 1:
+        apply_two(m, lo, g, chi_max, cutoff, floor_rel, gap_rel=gap_rel, regauge=regauge)
         return
-    # ring bond (n-1, 0): route site n-1 next to site 0 by swaps
-    assert t.a == n - 1 and t.b == 0
-    for p in range(n - 2, 0, -1):
-        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel,
-                  regauge=regauge)
-    # chain bond (0, 1) now holds (site 0, site n-1): reorder the gate basis
-    g01 = gates.SWAP @ g @ gates.SWAP
-    apply_two(m, 0, g01, chi_max, cutoff, floor_rel, gap_rel=gap_rel, regauge=regauge)
-    for p in range(1, n - 1):
-        apply_two(m, p, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel,
-                  regauge=regauge)
+    assert hi - lo == 2
+    # bring the site at hi next to lo, apply the gate, move it back
+    apply_two(m, lo + 1, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel,
+              regauge=regauge)
+    apply_two(m, lo, g, chi_max, cutoff, floor_rel, gap_rel=gap_rel, regauge=regauge)
+    apply_two(m, lo + 1, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel,
+              regauge=regauge)
 
 
 def expect_z(m: MPS) -> np.ndarray:
-    """<Z_i> / <psi|psi> for all sites by left and right environments,
+    """<Z_i> / <psi|psi> for every ring site i (chain position pos[i]), by
+    left and right environments,
     contracted pairwise:
       L_{i+1}[c,d] = sum_{a,b,s} L_i[a,b] conj(A[a,s,c]) A[b,s,d]
       R_i[a,b]     = sum_{c,d,s} conj(A[a,s,c]) A[b,s,d] R_{i+1}[c,d]
@@ -242,7 +268,7 @@ def expect_z(m: MPS) -> np.ndarray:
         T = np.tensordot(Lenv[i], A, axes=(1, 0))                    # [a,s,d]
         T2 = np.tensordot(T, Renv[i + 1], axes=(2, 1))              # [a,s,c]
         out[i] = np.sum(A.conj() * ZDIAG[None, :, None] * T2).real / norm
-    return out
+    return out[np.array(m.pos)]
 
 
 def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,

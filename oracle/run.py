@@ -36,8 +36,8 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
             z = sv.run_events(prob.init_bits, plan, ev, snaps)
             stats.append({})
         else:
-            m = (mps_mod.product_state(prob.init_bits) if init_tensors is None
-                 else mps_mod.canonicalize(init_tensors))
+            m = (mps_mod.product_state(prob.init_bits, prob.periodic) if init_tensors is None
+                 else mps_mod.canonicalize(init_tensors, prob.periodic))
             z = mps_mod.run_events(m, plan, ev, snaps, par.chi_max, par.cutoff, floor_rel, gap_rel,
                                    regauge)
             stats.append(m.stats)

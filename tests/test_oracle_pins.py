@@ -343,3 +343,13 @@ def test_regauge_leaves_untruncated_results_unchanged():
     b = R.run(prob, par, regauge=True)
     assert np.max(np.abs(a["v"] - b["v"])) < 1e-12
     assert sum(s["qr_moves"] for s in b["stats"]) > sum(s["qr_moves"] for s in a["stats"])
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 8, 9, 64])
+def test_folded_ring_order_keeps_bonds_within_distance_two(n):
+    order = M.chain_order(n, True)
+    assert sorted(order) == list(range(n))
+    pos = {s: p for p, s in enumerate(order)}
+    for i in range(n):
+        assert abs(pos[i] - pos[(i + 1) % n]) <= 2
+    assert M.chain_order(n, False) == list(range(n))
