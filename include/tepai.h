@@ -88,9 +88,12 @@ typedef struct {
 } tepai_params;
 
 /* Optional initial MPS shared by all samples (a "hybrid" start). Site tensors
- * A_i[d_i][2][d_{i+1}] are row-major, complex interleaved (re, im), and
- * concatenated over sites. They need not be normalised or canonical: every
- * sample first brings them to right-canonical form. */
+ * A_p[d_p][2][d_{p+1}] are row-major, complex interleaved (re, im), and
+ * concatenated over CHAIN positions p: natural site order for an open chain,
+ * and for a ring the folded order 0, n-1, 1, n-2, 2, ... that the library
+ * stores rings in (every ring bond within two chain positions). They need not
+ * be normalised or canonical: every sample first brings them to right-canonical
+ * form. */
 typedef struct {
     const int *bond_dims;          /* length n+1, bond_dims[0] = bond_dims[n] = 1, each <= chi_max */
     const double *tensors;         /* host (tepai_run) or device (tepai_dev_*) */

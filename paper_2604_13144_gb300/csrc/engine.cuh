@@ -133,6 +133,20 @@ struct Engine {
   __device__ void qr_right();
   __device__ void qr_left();
   __device__ void householder(C* Y, int m, int nq, C* Q, double tiny2);
+  __device__ void householder_blocked(C* Y, int m, int nq, C* Q, double tiny2);
+  __device__ void panel_t(const C* V, int m, int j0, int bp, C* T);
+  __device__ void apply_block_reflector(const C* V, int m, int j0, int bp, const C* T, bool herm,
+                                        C* G, int c0, int c1, C* CH, C* Wm);
+  // QR of Y (global or shared): blocked when Y is in global memory and the
+  // staging buffer holds a panel and a chunk
+  __device__ void qr_factor(C* Y, int m, int nq, C* Q, double tiny2) {
+    const C* xs = reinterpret_cast<const C*>(sm.x);
+    const bool y_in_smem = Y >= xs && Y < xs + a.smem_x_elems;
+    if (!y_in_smem && m >= 64 && (size_t)m * 32 + 512 <= (size_t)a.smem_x_elems)
+      householder_blocked(Y, m, nq, Q, tiny2);
+    else
+      householder(Y, m, nq, Q, tiny2);
+  }
   // two-site update on bond (i, i+1) with gate g (basis |s_i s_{i+1}>)
   __device__ void two_site(int i, const C g[16], bool end_left, bool is_swap);
   __device__ void form_theta(int i, const C g[16], bool end_left, bool zh, C* X);

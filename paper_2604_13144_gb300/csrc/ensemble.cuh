@@ -8,7 +8,7 @@
 namespace tepai {
 
 template <typename R>
-__device__ void Engine<R>::init_product() {
+__device__ __noinline__ void Engine<R>::init_product() {
   for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = 1;
   for (int i = tid(); i < a.n; i += nt()) {
     C* p = S(i);
@@ -26,7 +26,7 @@ __device__ void Engine<R>::init_product() {
 // unnormalised input grows geometrically along the chain and would overflow
 // FP32 long before site 0.
 template <typename R>
-__device__ void Engine<R>::init_from_tensors() {
+__device__ __noinline__ void Engine<R>::init_from_tensors() {
   for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = a.init_dims[i];
   __syncthreads();
   for (int i = 0; i <= a.n; ++i)
@@ -50,7 +50,7 @@ __device__ void Engine<R>::init_from_tensors() {
 
 // Rescale the centre tensor (and so the state) to unit norm.
 template <typename R>
-__device__ void Engine<R>::normalise_centre() {
+__device__ __noinline__ void Engine<R>::normalise_centre() {
   if (failed()) return;
   const int c = centre;
   const int cnt = sm.dims[c] * 2 * sm.dims[c + 1];
@@ -65,7 +65,7 @@ __device__ void Engine<R>::normalise_centre() {
 }
 
 template <typename R>
-__device__ void Engine<R>::apply_1site(int i, const C u[4]) {
+__device__ __noinline__ void Engine<R>::apply_1site(int i, const C u[4]) {
   PhaseTimer pt(st, PH_SINGLE);
   const int dl = sm.dims[i], dr = sm.dims[i + 1];
   C* p = S(i);
@@ -91,11 +91,12 @@ template <typename R> __device__ __forceinline__ void pauli2(int p, cplx<R> u[4]
 // Event (j, k, v): v = 1 setting B, 2 setting C, 3 deterministic Trotter gate.
 // Setting C is R_k(pi) = -i h_k, applied as the Pauli string h_k (the global
 // phase drops out of every expectation value) and flips sign(g_l) (App. B).
-// A two-site rotation on the ring bond (n-1, 0) is routed: site n-1 is swapped
-// left to position 1, the gate acts on chain bond (0, 1), and the site is
-// swapped back; every swap is a truncated two-site update.
+// Sites are chain positions: a ring is stored in the folded order 0, n-1, 1,
+// n-2, ..., so a bond term joins positions one or two apart. A gate two apart
+// swaps the far site next to the near one, acts, and swaps it back; every swap
+// is a truncated two-site update.
 template <typename R>
-__device__ void Engine<R>::apply_event(int k, int v, int& sign_count) {
+__device__ __noinline__ void Engine<R>::apply_event(int k, int v, int& sign_count) {
   if (failed()) return;
   const TermDev& T = a.terms[k];
   if (tid() == 0) st.events++;
@@ -116,31 +117,25 @@ __device__ void Engine<R>::apply_event(int k, int v, int& sign_count) {
   }
   C g[16];
   for (int q = 0; q < 16; ++q) g[q] = C{(R)T.g[2 * q], (R)T.g[2 * q + 1]};
+  // sites are chain positions with T.a < T.b and the gate in basis |s_a s_b>
   if (T.b == T.a + 1) { two_site(T.a, g, false, false); return; }
-  // ring bond: T.a == n-1, T.b == 0
+  if (T.b != T.a + 2) { fail(ST_BAD_DIM, 10000 + k); return; }
+  // two positions apart: bring the site at a+2 next to a, apply, move it back
   C sw[16];
   for (int q = 0; q < 16; ++q) sw[q] = C{0, 0};
   sw[0] = C{1, 0}; sw[6] = C{1, 0}; sw[9] = C{1, 0}; sw[15] = C{1, 0};
-  const int n = a.n;
-  for (int p = n - 2; p >= 1; --p) two_site(p, sw, true, true);
-  // chain bond (0, 1) holds (site 0, site n-1): reorder the gate basis
-  C g2[16];
-  for (int st4 = 0; st4 < 4; ++st4)
-    for (int q = 0; q < 4; ++q) {
-      const int st_sw = ((st4 & 1) << 1) | (st4 >> 1), q_sw = ((q & 1) << 1) | (q >> 1);
-      g2[st4 * 4 + q] = g[st_sw * 4 + q_sw];
-    }
-  two_site(0, g2, false, false);
-  for (int p = 1; p <= n - 2; ++p) two_site(p, sw, false, true);
+  two_site(T.a + 1, sw, true, true);
+  two_site(T.a, g, false, false);
+  two_site(T.a + 1, sw, false, true);
 }
 
-// <Z_i> / <psi|psi> for all sites. With the centre on site c, sites left of c
+// <Z_p> / <psi|psi> for every chain position p. With the centre on site c, sites left of c
 // are left-orthonormal and sites right of c are right-orthonormal, so a
 // transfer-matrix sweep rightward from c (E <- sum_s A^s^H E A^s) gives
 // <Z_i> for i >= c and a sweep leftward from c (F <- sum_s A^s F A^s^H) gives
 // <Z_i> for i < c.
 template <typename R>
-__device__ void Engine<R>::measure_z(double* zout) {
+__device__ __noinline__ void Engine<R>::measure_z(double* zout) {
   if (failed()) return;
   PhaseTimer pt(st, PH_MEASURE);
   const int n = a.n, c = centre;

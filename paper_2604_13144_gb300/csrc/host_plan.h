@@ -24,6 +24,7 @@ struct FixedVec {
   const T* data() const { return buf; }
   size_t size() const { return n; }
   const T& operator[](size_t i) const { return buf[i]; }
+  T& operator[](size_t i) { return buf[i]; }
 };
 
 template <template <typename> class Vec>
@@ -41,6 +42,7 @@ struct PlanT {
     terms.clear(); snaps.clear(); gnorm.clear(); obs.clear(); bits.clear();
   }
   bool overflowed() const;
+  void bits_set(int p, unsigned char v) { if ((size_t)p < bits.size()) bits[p] = v; }
 };
 
 template <typename T> using HeapVec = std::vector<T>;
@@ -93,6 +95,26 @@ inline void rotation_gate(int pauli, bool two_site, double phi, double* g) {
     }
 }
 
+// Chain position of ring site `site`: natural order for an open chain; for a
+// ring the folded order 0, n-1, 1, n-2, 2, ... (every ring bond within chain
+// distance 2, every cut crossing two ring bonds).
+inline int chain_pos(int site, int n, bool periodic) {
+  if (!periodic) return site;
+  return site <= (n - 1) / 2 ? 2 * site : 2 * (n - 1 - site) + 1;
+}
+
+// The same gate in the basis |s_b s_a> instead of |s_a s_b>.
+inline void swap_gate_basis(double* g) {
+  double t[32];
+  for (int r = 0; r < 4; ++r)
+    for (int q = 0; q < 4; ++q) {
+      const int rs = ((r & 1) << 1) | (r >> 1), qs = ((q & 1) << 1) | (q >> 1);
+      t[2 * (r * 4 + q)] = g[2 * (rs * 4 + qs)];
+      t[2 * (r * 4 + q) + 1] = g[2 * (rs * 4 + qs) + 1];
+    }
+  for (int e = 0; e < 32; ++e) g[e] = t[e];
+}
+
 template <class Plan>
 inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   if (!P || !Q) return TEPAI_ERR_INVALID_ARG;
@@ -116,13 +138,15 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
     if (Q->n_obs < 1) return TEPAI_ERR_INVALID_ARG;
     for (int o = 0; o < Q->n_obs; ++o) {
       if (Q->obs_sites[o] < 0 || Q->obs_sites[o] >= n) return TEPAI_ERR_INVALID_ARG;
-      hp.obs.push_back(Q->obs_sites[o]);
+      hp.obs.push_back(chain_pos(Q->obs_sites[o], n, P->periodic));
     }
   } else {
-    for (int i = 0; i < n; ++i) hp.obs.push_back(i);
+    for (int i = 0; i < n; ++i) hp.obs.push_back(chain_pos(i, n, P->periodic));
   }
   hp.n_obs = (int)hp.obs.size();
-  for (int i = 0; i < n; ++i) hp.bits.push_back(P->init_bits[i] ? 1 : 0);
+  // initial bits in chain order
+  for (int p = 0; p < n; ++p) hp.bits.push_back(0);
+  for (int i = 0; i < n; ++i) hp.bits_set(chain_pos(i, n, P->periodic), P->init_bits[i] ? 1 : 0);
   // term list: Z_0..Z_{n-1}, then per bond b: XX_b, YY_b, ZZ_b
   struct T0 { int kind, a, b, pauli; double c; };
   hp.L = n + 3 * nb;
@@ -165,6 +189,13 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
     td.thr_event = threshold_u64(q);
     td.thr_c = threshold_u64(r);
     rotation_gate(t.pauli, t.kind == 1, phi, td.g);
+    // sites as chain positions; a bond gate in the basis |s_lower s_upper>
+    td.a = chain_pos(t.a, n, P->periodic);
+    td.b = chain_pos(t.b, n, P->periodic);
+    if (t.kind == 1 && td.a > td.b) {
+      const int tmp = td.a; td.a = td.b; td.b = tmp;
+      swap_gate_basis(td.g);
+    }
     hp.terms.push_back(td);
     sumq += q;
     gstep *= gn;

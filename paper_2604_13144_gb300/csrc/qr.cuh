@@ -15,7 +15,7 @@ namespace tepai {
 // amplitudes like sin(Delta/2)^k whose squares underflow FP32, and the scale
 // would overflow.
 template <typename R>
-__device__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, double tiny2) {
+__device__ __noinline__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, double tiny2) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int r = min(m, nq);
   C* vhead = reinterpret_cast<C*>(sm.hh);
@@ -100,7 +100,7 @@ __device__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, double tiny2) 
 
 // Centre c -> c+1: A_c (2 d_c x d_{c+1}) = Q R; A_c <- Q, A_{c+1} <- R A_{c+1}.
 template <typename R>
-__device__ void Engine<R>::qr_right() {
+__device__ __noinline__ void Engine<R>::qr_right() {
   PhaseTimer pt(st, PH_QR);
   const int c = centre;
   if (c < 0 || c > a.n - 2) { fail(ST_BAD_DIM, 3000 + c); return; }
@@ -115,7 +115,7 @@ __device__ void Engine<R>::qr_right() {
     Y[(size_t)b * m + row] = Ac[e];
   }
   __syncthreads();
-  householder(Y, m, nq, Q, 0.0);
+  qr_factor(Y, m, nq, Q, 0.0);
   C* Acw = S(c);
   for (int e = tid(); e < m * r; e += nt()) {
     const int row = e / r, col = e - row * r;
@@ -143,7 +143,7 @@ __device__ void Engine<R>::qr_right() {
 // Centre c -> c-1: A_c (d_c x 2 d_{c+1}) = L Q via A_c^H = Q' R;
 // A_c <- Q'^H (right-orthonormal rows), A_{c-1} <- A_{c-1} R^H.
 template <typename R>
-__device__ void Engine<R>::qr_left() {
+__device__ __noinline__ void Engine<R>::qr_left() {
   PhaseTimer pt(st, PH_QR);
   const int c = centre;
   if (c < 1 || c > a.n - 1) { fail(ST_BAD_DIM, 5000 + c); return; }
@@ -155,7 +155,7 @@ __device__ void Engine<R>::qr_left() {
   const C* Ac = S(c);
   for (int e = tid(); e < m * nq; e += nt()) { const C v = Ac[e]; Y[e] = C{v.re, -v.im}; }
   __syncthreads();
-  householder(Y, m, nq, Q, 0.0);
+  qr_factor(Y, m, nq, Q, 0.0);
   C* Acw = S(c);
   for (int e = tid(); e < r * m; e += nt()) { const C v = Q[e]; Acw[e] = C{v.re, -v.im}; }
   __syncthreads();
@@ -186,6 +186,222 @@ template <typename R>
 __device__ void Engine<R>::move_centre(int target) {
   while (centre < target && !failed()) qr_right();
   while (centre > target && !failed()) qr_left();
+}
+
+}  // namespace tepai
+
+namespace tepai {
+
+// Compact WY factor of the panel (Schreiber & Van Loan, SIAM J. Sci. Stat.
+// Comput. 10, 1989): H_{j0} ... H_{j0+bp-1} = I - V T V^H with T upper
+// triangular, T_kk = tau_k, T_{0:k,k} = -tau_k T_{0:k,0:k} (V_{:,0:k}^H v_k).
+template <typename R>
+__device__ __noinline__ void Engine<R>::panel_t(const C* V, int m, int j0, int bp, C* T) {
+  const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
+  const C* tau = reinterpret_cast<const C*>(sm.hh) + 2 * cap;
+  // z_{k,jj} = V_{:,k}^H v_jj for k < jj, stored in T[k][jj] (T row-major 16 x 16)
+  for (int e = w; e < bp * bp; e += nw) {
+    const int k = e / bp, jj = e - k * bp;
+    if (k >= jj) continue;
+    const C* vk = V + (size_t)k * m;
+    const C* vj = V + (size_t)jj * m;
+    R sr = 0, si = 0;
+    for (int row = j0 + jj + lane; row < m; row += 32) {
+      const C a = vk[row], b = vj[row];
+      sr = fma(a.re, b.re, fma(a.im, b.im, sr));
+      si = fma(a.re, b.im, fma(-a.im, b.re, si));
+    }
+    sr = warp_sum(sr); si = warp_sum(si);
+    if (lane == 0) T[k * 16 + jj] = C{sr, si};
+  }
+  __syncthreads();
+  if (tid() == 0) {
+    for (int jj = 0; jj < bp; ++jj) {
+      const R tj = tau[j0 + jj].re;
+      C tmp[16];
+      for (int k = 0; k < jj; ++k) {
+        C acc = {0, 0};
+        for (int q = k; q < jj; ++q) fma_c(acc, T[k * 16 + q], T[q * 16 + jj]);
+        tmp[k] = C{-tj * acc.re, -tj * acc.im};
+      }
+      for (int k = 0; k < jj; ++k) T[k * 16 + jj] = tmp[k];
+      T[jj * 16 + jj] = C{tj, 0};
+      for (int k = jj + 1; k < 16; ++k) T[k * 16 + jj] = C{0, 0};
+    }
+  }
+  __syncthreads();
+}
+
+// Apply I - V op(T) V^H to columns [c0, c1) of the global matrix G (ld m),
+// rows j0..m-1, in shared-memory chunks of 16 columns: W = V^H C,
+// W <- op(T) W (T^H when herm), C <- C - V W. V is dense in shared memory
+// (V[k*m + row], zero above its diagonal, vhead on it).
+template <typename R>
+__device__ void Engine<R>::apply_block_reflector(const C* V, int m, int j0, int bp, const C* T, bool herm,
+                                                 C* G, int c0, int c1, C* CH, C* Wm) {
+  const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
+  for (int cs = c0; cs < c1; cs += 16) {
+    const int cb = min(16, c1 - cs);
+    for (int e = tid(); e < cb * m; e += nt()) {
+      const int c = e / m, row = e - c * m;
+      if (row >= j0) CH[(size_t)c * m + row] = G[(size_t)(cs + c) * m + row];
+    }
+    __syncthreads();
+    for (int e = w; e < bp * cb; e += nw) {
+      const int k = e / cb, c = e - k * cb;
+      const C* vk = V + (size_t)k * m;
+      const C* x = CH + (size_t)c * m;
+      R sr = 0, si = 0;
+      for (int row = j0 + k + lane; row < m; row += 32) {
+        const C a = vk[row], b = x[row];
+        sr = fma(a.re, b.re, fma(a.im, b.im, sr));
+        si = fma(a.re, b.im, fma(-a.im, b.re, si));
+      }
+      sr = warp_sum(sr); si = warp_sum(si);
+      if (lane == 0) Wm[k * 16 + c] = C{sr, si};
+    }
+    __syncthreads();
+    // W2 = op(T) W, kept in registers of threads (k, c), then written back
+    C w2 = {0, 0};
+    const int kk = tid() / 16, cc = tid() % 16;
+    const bool act = tid() < 256 && kk < bp && cc < cb;
+    if (act) {
+      if (herm) {
+        for (int q = 0; q <= kk; ++q) fma_cc(w2, T[q * 16 + kk], Wm[q * 16 + cc]);
+      } else {
+        for (int q = kk; q < bp; ++q) fma_c(w2, T[kk * 16 + q], Wm[q * 16 + cc]);
+      }
+    }
+    __syncthreads();
+    if (act) Wm[kk * 16 + cc] = w2;
+    __syncthreads();
+    for (int e = tid(); e < cb * m; e += nt()) {
+      const int c = e / m, row = e - c * m;
+      if (row < j0) continue;
+      C x = CH[(size_t)c * m + row];
+      const int kmax = min(bp, row - j0 + 1);
+      for (int k = 0; k < kmax; ++k) {
+        const C vk = V[(size_t)k * m + row];
+        const C wv = Wm[k * 16 + c];
+        x.re -= vk.re * wv.re - vk.im * wv.im;
+        x.im -= vk.re * wv.im + vk.im * wv.re;
+      }
+      G[(size_t)(cs + c) * m + row] = x;
+    }
+    __syncthreads();
+  }
+}
+
+// Turn the factored panel in P (rows >= j0 of columns j0..j0+bp-1) into the
+// dense reflector block V: zero above each diagonal, vhead on it.
+template <typename R>
+__device__ __forceinline__ void densify_panel(cplx<R>* P, const cplx<R>* vhead, int m, int j0, int bp) {
+  for (int e = threadIdx.x; e < bp * m; e += blockDim.x) {
+    const int k = e / m, row = e - k * m;
+    const int d = j0 + k;
+    if (row < d) P[e] = cplx<R>{0, 0};
+    else if (row == d) P[e] = vhead[d];
+  }
+  __syncthreads();
+}
+
+// Blocked Householder QR of Y (m x nq, column-major, global memory): 16-column
+// panels are factored in shared memory, then the trailing columns are updated
+// with the panel's block reflector. Same output convention as householder().
+template <typename R>
+__device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq, C* Q, double tiny2) {
+  const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
+  const int r = min(m, nq);
+  C* vhead = reinterpret_cast<C*>(sm.hh);
+  C* tau = vhead + 2 * cap;
+  C* alpha = tau + 2 * cap;
+  C* P = reinterpret_cast<C*>(sm.x);
+  C* CH = P + (size_t)m * 16;
+  C* T = CH + (size_t)m * 16;
+  C* Wm = T + 256;
+  for (int j0 = 0; j0 < r; j0 += 16) {
+    const int bp = min(16, r - j0);
+    for (int e = tid(); e < bp * m; e += nt()) {
+      const int c = e / m, row = e - c * m;
+      if (row >= j0) P[(size_t)c * m + row] = Y[(size_t)(j0 + c) * m + row];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < bp; ++jj) {
+      const int j = j0 + jj;
+      if (w == 0) {
+        const C* y = P + (size_t)jj * m;
+        R nr2 = 0;
+        for (int row = j + lane; row < m; row += 32) nr2 += abs2(y[row]);
+        nr2 = warp_sum(nr2);
+        if (lane == 0) {
+          const C x0 = y[j];
+          const R ax0 = sqrt(abs2(x0));
+          const R nrm = sqrt(nr2);
+          const R tj = R(1) / (nrm * (nrm + ax0));
+          if (!((double)nr2 > tiny2) || !(nrm > R(0)) || !isfinite(tj)) {
+            vhead[j] = C{1, 0}; tau[j] = C{0, 0}; alpha[j] = x0;
+          } else {
+            const C ph = ax0 > R(0) ? C{x0.re / ax0, x0.im / ax0} : C{1, 0};
+            alpha[j] = C{-ph.re * nrm, -ph.im * nrm};
+            vhead[j] = C{ph.re * (ax0 + nrm), ph.im * (ax0 + nrm)};
+            tau[j] = C{tj, 0};
+          }
+        }
+      }
+      __syncthreads();
+      const C vh = vhead[j];
+      const R tj = tau[j].re;
+      if (tj != R(0)) {
+        const C* vj = P + (size_t)jj * m;
+        for (int c = jj + 1 + w; c < bp; c += nw) {
+          C* y = P + (size_t)c * m;
+          R sr = 0, si = 0;
+          for (int row = j + lane; row < m; row += 32) {
+            const C vv = row == j ? vh : vj[row];
+            const C yy = y[row];
+            sr = fma(vv.re, yy.re, fma(vv.im, yy.im, sr));
+            si = fma(vv.re, yy.im, fma(-vv.im, yy.re, si));
+          }
+          sr = warp_sum(sr) * tj; si = warp_sum(si) * tj;
+          const C sc = {sr, si};
+          for (int row = j + lane; row < m; row += 32) {
+            const C vv = row == j ? vh : vj[row];
+            y[row] = sub(y[row], mul(vv, sc));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = tid(); e < bp * m; e += nt()) {
+      const int c = e / m, row = e - c * m;
+      if (row >= j0) Y[(size_t)(j0 + c) * m + row] = P[(size_t)c * m + row];
+    }
+    __syncthreads();
+    if (j0 + bp < nq) {
+      densify_panel(P, vhead, m, j0, bp);
+      panel_t(P, m, j0, bp, T);
+      apply_block_reflector(P, m, j0, bp, T, true, Y, j0 + bp, nq, CH, Wm);
+    }
+  }
+  if (Q == nullptr) return;
+  for (int e = tid(); e < m * r; e += nt()) {
+    const int col = e / m, row = e - col * m;
+    Q[e] = C{row == col ? R(1) : R(0), 0};
+  }
+  __syncthreads();
+  const int last = ((r - 1) / 16) * 16;
+  for (int j0 = last; j0 >= 0; j0 -= 16) {
+    const int bp = min(16, r - j0);
+    for (int e = tid(); e < bp * m; e += nt()) {
+      const int c = e / m, row = e - c * m;
+      if (row >= j0) P[(size_t)c * m + row] = Y[(size_t)(j0 + c) * m + row];
+    }
+    __syncthreads();
+    densify_panel(P, vhead, m, j0, bp);
+    panel_t(P, m, j0, bp, T);
+    apply_block_reflector(P, m, j0, bp, T, false, Q, j0, r, CH, Wm);
+  }
+  (void)alpha;
 }
 
 }  // namespace tepai

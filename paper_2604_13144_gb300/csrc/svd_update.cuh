@@ -13,7 +13,7 @@ namespace tepai {
 // left. With zh set, X receives Z^H instead (the input of the preconditioning
 // QR): theta'^H (ld 2dr) or conj(theta') (ld 2dl).
 template <typename R>
-__device__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, bool zh, C* X) {
+__device__ __noinline__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, bool zh, C* X) {
   const int dl = sm.dims[i], dc = sm.dims[i + 1], dr = sm.dims[i + 2];
   const C* A = S(i);
   const C* B = S(i + 1);
@@ -106,7 +106,7 @@ __device__ __forceinline__ bool rotate_pair_m(cplx<R>* xp, cplx<R>* xq, int m, R
 // 1985): nc-1 rounds of disjoint pairs, one warp per pair. Rotations are
 // counted in ibuf[0].
 template <typename R>
-__device__ void Engine<R>::rr_pass(C* X, int m, int nc, R tol, R thr) {
+__device__ __noinline__ void Engine<R>::rr_pass(C* X, int m, int nc, R tol, R thr) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int np = nc + (nc & 1);
   for (int r = 0; r < np - 1; ++r) {
@@ -124,7 +124,7 @@ __device__ void Engine<R>::rr_pass(C* X, int m, int nc, R tol, R thr) {
 
 // All pairs (p in block A, q in block B): round r pairs p with (p + r) mod nmax.
 template <typename R>
-__device__ void Engine<R>::cross_pass(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
+__device__ __noinline__ void Engine<R>::cross_pass(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int nmax = max(na, nb);
   for (int r = 0; r < nmax; ++r) {
@@ -147,7 +147,7 @@ __device__ void Engine<R>::cross_pass(C* XA, int na, C* XB, int nb, int m, R tol
 // is visited once per sweep. Sweeps stop when one rotates nothing; ibuf[1] = 1
 // then, 0 if the sweep cap was hit.
 template <typename R>
-__device__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_smem) {
+__device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_smem) {
   // rotate a pair when |x_p^H x_q| > tol |x_p||x_q|, tol = a.tol * sqrt(m): the
   // rounding noise of a length-m dot product grows like sqrt(m) eps, so a fixed
   // tolerance would leave the last sweeps rotating pairs on noise alone
@@ -217,7 +217,7 @@ __device__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_smem) {
 // such k' >= 1 exists.
 // The kept values are rescaled to unit norm, so every sample stays normalised.
 template <typename R>
-__device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is_swap) {
+__device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is_swap) {
   if (failed()) return;
   if (i < 0 || i > a.n - 2) { fail(ST_BAD_DIM, i); return; }
   if (centre < i) move_centre(i);
@@ -250,7 +250,7 @@ __device__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is
       fro = block_sum(fro, sm.red);
       // skip only reflectors whose 1/|x|^2 scale would overflow; smaller
       // columns are still rotated exactly (dropping them would lose their weight)
-      householder(Y, nc, m, nullptr, (sizeof(R) == 4 ? 1e-30 : 1e-280) * fro);
+      qr_factor(Y, nc, m, nullptr, (sizeof(R) == 4 ? 1e-30 : 1e-280) * fro);
       const C* alpha = reinterpret_cast<const C*>(sm.hh) + 4 * cap;
       X = x_smem ? xs : XG;
       if (X == Y) {
