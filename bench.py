@@ -242,6 +242,7 @@ def run_ours(a):
     t0 = time.perf_counter()
     upd, flops, kms, events, sweeps = 0.0, 0.0, 0.0, 0.0, 0.0
     phases = {}
+    grid = 1
     nconv, maxchi = 0, 0
     for i in range(a.steps):
         ms, st = step(a.warmup + i)
@@ -250,6 +251,7 @@ def run_ours(a):
         flops += st["alg_flops"]
         events += st["events"]
         sweeps += st["jacobi_sweeps"]
+        grid = st["grid_ctas"]
         for k, v in st["phase_cycles"].items():
             phases[k] = phases.get(k, 0.0) + v
         nconv += st["n_not_converged"]
@@ -312,6 +314,7 @@ def run_ours(a):
         "stats": {"events_per_s": events / elapsed, "updates": upd, "alg_flops": flops,
                   "sweeps_per_svd": sweeps / max(upd, 1.0),
                   "phase_share": {k: round(v / max(sum(phases.values()), 1.0), 4) for k, v in phases.items()},
+                  "cta_busy_frac": sum(phases.values()) / max(kms / 1e3 * SM_MAX_MHZ * 1e6 * grid, 1.0),
                   "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi},
     }
     if not a.no_tts and world == 1:

@@ -113,6 +113,7 @@ typedef struct {
     double phase_cycles[8];        /* SM cycles per phase, summed over CTAs: init, sampler,
                                       single-site gates, theta, Jacobi SVD, truncation and
                                       write-back, centre moves (QR), measurement */
+    int grid_ctas;                 /* CTAs of the ensemble launch */
 } tepai_stats;
 
 /* Circuit event of one sample: Trotter step j (1-based), term k, setting v

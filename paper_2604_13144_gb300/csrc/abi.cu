@@ -248,6 +248,7 @@ int stats_impl(void* ws, tepai_stats* out, cudaStream_t st) {
   out->max_chi = ds.max_chi;
   out->n_not_converged = (int)ds.not_converged;
   for (int p = 0; p < PH_N; ++p) out->phase_cycles[p] = (double)ds.cycles[p];
+  out->grid_ctas = pr.grid;
   return TEPAI_OK;
 }
 

@@ -153,6 +153,8 @@ struct Engine {
   __device__ int jacobi(C* X, int m, int nc, bool x_in_smem);
   __device__ void rr_pass(C* X, int m, int nc, R tol, R thr);
   __device__ void cross_pass(C* XA, int na, C* XB, int nb, int m, R tol, R thr);
+  template <int RPL>
+  __device__ void cross_pass_regs(C* XA, int na, C* XB, int nb, int m, R tol, R thr);
   // events
   __device__ void apply_event(int k, int v, int& sign_count);
   // measurement

@@ -138,6 +138,113 @@ __device__ __noinline__ void Engine<R>::cross_pass(C* XA, int na, C* XB, int nb,
   }
 }
 
+// Rotation parameters of a pair from its Gram entries (al = |x_p|^2,
+// be = |x_q|^2, g = x_p^H x_q = gr + i gi). Returns false when no rotation is
+// due; otherwise c, s and e^{-i phi} = (er, ei).
+template <typename R>
+__device__ __forceinline__ bool rot_params(R al, R be, R gr, R gi, R tol, R thr, R& c, R& s, R& er, R& ei) {
+  if (al < thr || be < thr) return false;
+  const R g = sqrt(gr * gr + gi * gi);
+  if (!(g > tol * sqrt(al * be))) return false;
+  const R zeta = (be - al) / (R(2) * g);
+  const R az = fabs(zeta);
+  R tt = az > R(1) ? R(1) / (az * (R(1) + sqrt(R(1) + R(1) / (az * az))))
+                   : R(1) / (az + sqrt(R(1) + az * az));
+  if (zeta < R(0)) tt = -tt;
+  c = rsqrt_<R>(R(1) + tt * tt);
+  s = c * tt;
+  er = gr / g;
+  ei = -gi / g;
+  return true;
+}
+
+// Cross pairs of blocks A and B (na, nb <= 2 * warps) with the warp-owned A
+// columns held in registers: warp w owns A columns w and w + nw for the whole
+// pass; in round r they meet B columns (p + r) mod nmax. Only B columns move
+// through shared memory, and the two pairs of a warp are processed together.
+template <typename R>
+template <int RPL>
+__device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
+  const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
+  const int nmax = max(na, nb);
+  const int p0 = w, p1 = w + nw;
+  const bool h0 = p0 < na, h1 = p1 < na;
+  C a0[RPL], a1[RPL], b0[RPL], b1[RPL];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int row = lane + 32 * t;
+    a0[t] = (h0 && row < m) ? XA[(size_t)p0 * m + row] : C{0, 0};
+    a1[t] = (h1 && row < m) ? XA[(size_t)p1 * m + row] : C{0, 0};
+  }
+  int rot = 0;
+  for (int r = 0; r < nmax; ++r) {
+    const int q0 = (p0 + r) % nmax, q1 = (p1 + r) % nmax;
+    const bool d0 = h0 && q0 < nb, d1 = h1 && q1 < nb;
+    C* xb0 = XB + (size_t)q0 * m;
+    C* xb1 = XB + (size_t)q1 * m;
+    R al0 = 0, be0 = 0, gr0 = 0, gi0 = 0, al1 = 0, be1 = 0, gr1 = 0, gi1 = 0;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int row = lane + 32 * t;
+      b0[t] = (d0 && row < m) ? xb0[row] : C{0, 0};
+      b1[t] = (d1 && row < m) ? xb1[row] : C{0, 0};
+      al0 = fma(a0[t].re, a0[t].re, fma(a0[t].im, a0[t].im, al0));
+      be0 = fma(b0[t].re, b0[t].re, fma(b0[t].im, b0[t].im, be0));
+      gr0 = fma(a0[t].re, b0[t].re, fma(a0[t].im, b0[t].im, gr0));
+      gi0 = fma(a0[t].re, b0[t].im, fma(-a0[t].im, b0[t].re, gi0));
+      al1 = fma(a1[t].re, a1[t].re, fma(a1[t].im, a1[t].im, al1));
+      be1 = fma(b1[t].re, b1[t].re, fma(b1[t].im, b1[t].im, be1));
+      gr1 = fma(a1[t].re, b1[t].re, fma(a1[t].im, b1[t].im, gr1));
+      gi1 = fma(a1[t].re, b1[t].im, fma(-a1[t].im, b1[t].re, gi1));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      al0 += __shfl_xor_sync(0xffffffffu, al0, o); be0 += __shfl_xor_sync(0xffffffffu, be0, o);
+      gr0 += __shfl_xor_sync(0xffffffffu, gr0, o); gi0 += __shfl_xor_sync(0xffffffffu, gi0, o);
+      al1 += __shfl_xor_sync(0xffffffffu, al1, o); be1 += __shfl_xor_sync(0xffffffffu, be1, o);
+      gr1 += __shfl_xor_sync(0xffffffffu, gr1, o); gi1 += __shfl_xor_sync(0xffffffffu, gi1, o);
+    }
+    R c0, s0, er0, ei0, c1, s1, er1, ei1;
+    const bool r0 = d0 && rot_params<R>(al0, be0, gr0, gi0, tol, thr, c0, s0, er0, ei0);
+    const bool r1 = d1 && rot_params<R>(al1, be1, gr1, gi1, tol, thr, c1, s1, er1, ei1);
+    if (r0) {
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const C wv = {er0 * b0[t].re - ei0 * b0[t].im, er0 * b0[t].im + ei0 * b0[t].re};
+        const C u = a0[t];
+        a0[t] = C{c0 * u.re - s0 * wv.re, c0 * u.im - s0 * wv.im};
+        const C nb0 = {s0 * u.re + c0 * wv.re, s0 * u.im + c0 * wv.im};
+        const int row = lane + 32 * t;
+        if (row < m) xb0[row] = nb0;
+      }
+      ++rot;
+    }
+    if (r1) {
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const C wv = {er1 * b1[t].re - ei1 * b1[t].im, er1 * b1[t].im + ei1 * b1[t].re};
+        const C u = a1[t];
+        a1[t] = C{c1 * u.re - s1 * wv.re, c1 * u.im - s1 * wv.im};
+        const C nb1 = {s1 * u.re + c1 * wv.re, s1 * u.im + c1 * wv.im};
+        const int row = lane + 32 * t;
+        if (row < m) xb1[row] = nb1;
+      }
+      ++rot;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int row = lane + 32 * t;
+    if (row < m) {
+      if (h0) XA[(size_t)p0 * m + row] = a0[t];
+      if (h1) XA[(size_t)p1 * m + row] = a1[t];
+    }
+  }
+  if (lane == 0 && rot) atomicAdd(&sm.ibuf[0], rot);
+  __syncthreads();
+}
+
 // Cyclic one-sided Jacobi SVD (Hestenes, J. SIAM 6, 1958) on the columns of X
 // (m x nc, column-major). When X lives in shared memory, each sweep is one
 // round-robin pass. When it does not fit, X stays in global memory and is
@@ -163,16 +270,33 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
   if (tid() == 0) sm.ibuf[1] = 0;
   if (nc < 2) { __syncthreads(); if (tid() == 0) sm.ibuf[1] = 1; __syncthreads(); return 0; }
   C* xs = reinterpret_cast<C*>(sm.x);
+  const int nw = nt() >> 5;
+  // column blocks of bw: the width the staging buffer allows, at most 2 columns
+  // per warp so that a block's warp-owned columns fit in registers
   int bw = 1;
   if (!x_in_smem) {
     while (4 * bw * m <= a.smem_x_elems && 2 * bw < nc) bw *= 2;
+  } else {
+    bw = nc;
   }
-  const int nbk = x_in_smem ? 1 : (nc + bw - 1) / bw;
+  if (bw > 2 * nw) bw = 2 * nw;
+  const int nbk = (nc + bw - 1) / bw;
+  auto cross = [&](C* XA, int na, C* XB, int nbb) {
+    if (m <= 64) cross_pass_regs<2>(XA, na, XB, nbb, m, tol, thr);
+    else if (m <= 128) cross_pass_regs<4>(XA, na, XB, nbb, m, tol, thr);
+    else if (m <= 256) cross_pass_regs<8>(XA, na, XB, nbb, m, tol, thr);
+    else cross_pass(XA, na, XB, nbb, m, tol, thr);
+  };
   while (sweep < a.max_sweeps) {
     if (tid() == 0) sm.ibuf[0] = 0;
     __syncthreads();
     if (x_in_smem) {
-      rr_pass(X, m, nc, tol, thr);
+      for (int I = 0; I < nbk; ++I) {
+        const int nI = min(bw, nc - I * bw);
+        C* xI = X + (size_t)I * bw * m;
+        rr_pass(xI, m, nI, tol, thr);
+        for (int J = I + 1; J < nbk; ++J) cross(xI, nI, X + (size_t)J * bw * m, min(bw, nc - J * bw));
+      }
     } else {
       C* sa = xs;
       C* sb = xs + (size_t)bw * m;
@@ -187,7 +311,7 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
           C* gJ = X + (size_t)J * bw * m;
           for (int e = tid(); e < nJ * m; e += nt()) sb[e] = gJ[e];
           __syncthreads();
-          cross_pass(sa, nI, sb, nJ, m, tol, thr);
+          cross(sa, nI, sb, nJ);
           for (int e = tid(); e < nJ * m; e += nt()) gJ[e] = sb[e];
           __syncthreads();
         }

@@ -57,7 +57,8 @@ class Stats(C.Structure):
                 ("qr_moves", C.c_double), ("jacobi_sweeps", C.c_double),
                 ("max_discarded_weight", C.c_double), ("alg_flops", C.c_double),
                 ("max_chi", C.c_int), ("n_not_converged", C.c_int),
-                ("device_status", C.c_int * 3), ("phase_cycles", C.c_double * 8)]
+                ("device_status", C.c_int * 3), ("phase_cycles", C.c_double * 8),
+                ("grid_ctas", C.c_int)]
 
     PHASES = ("init", "sampler", "single_site", "theta", "jacobi", "truncate", "qr", "measure")
 
