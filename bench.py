@@ -240,7 +240,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     t0 = time.perf_counter()
-    upd, flops, kms, events, sweeps = 0.0, 0.0, 0.0, 0.0, 0.0
+    upd, flops, kms, events, sweeps, qrm = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0
     phases = {}
     grid = 1
     nconv, maxchi = 0, 0
@@ -251,6 +251,7 @@ def run_ours(a):
         flops += st["alg_flops"]
         events += st["events"]
         sweeps += st["jacobi_sweeps"]
+        qrm += st["qr_moves"]
         grid = st["grid_ctas"]
         for k, v in st["phase_cycles"].items():
             phases[k] = phases.get(k, 0.0) + v
@@ -313,6 +314,8 @@ def run_ours(a):
                      "peak_note": "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"},
         "stats": {"events_per_s": events / elapsed, "updates": upd, "alg_flops": flops,
                   "sweeps_per_svd": sweeps / max(upd, 1.0),
+                  "qr_moves_per_update": qrm / max(upd, 1.0),
+                  "updates_per_event": upd / max(events, 1.0),
                   "phase_share": {k: round(v / max(sum(phases.values()), 1.0), 4) for k, v in phases.items()},
                   "cta_busy_frac": sum(phases.values()) / max(kms / 1e3 * SM_MAX_MHZ * 1e6 * grid, 1.0),
                   "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi},

@@ -98,7 +98,7 @@ struct KArgs {
 
 // Device status codes. A CTA that detects a broken invariant records the first
 // failure, touches no more memory for that sample, and leaves the kernel.
-enum : int { ST_OK = 0, ST_BAD_DIM = 1, ST_BAD_RANK = 2, ST_NONFINITE = 3 };
+enum : int { ST_OK = 0, ST_BAD_DIM = 1, ST_BAD_RANK = 2, ST_NONFINITE = 3, ST_COPY_TIMEOUT = 4 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t al) { return (x + al - 1) / al * al; }
 
@@ -108,6 +108,7 @@ __host__ __device__ inline size_t smem_fixed_bytes(int n, int L, int cap, int cs
   b += align_up((size_t)(n + 1) * 4, 16);          // dims
   b += align_up((size_t)L, 16);                     // flags
   b += 64 * 8;                                      // red
+  b += 16;                                          // mbarrier of the bulk copies
   b += align_up((size_t)2 * cap * 8, 16);           // wn
   b += align_up((size_t)2 * cap * 4, 16);           // perm
   b += align_up((size_t)n * 8, 16);                 // zval

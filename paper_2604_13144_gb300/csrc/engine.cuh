@@ -71,11 +71,42 @@ struct PhaseTimer {
   }
 };
 
+// Bulk copies between global and shared memory through the copy engine
+// (cp.async.bulk, sm_90+): a load completes on an mbarrier with a byte count,
+// a store completes as a bulk async-group. Addresses 16-byte aligned, sizes
+// multiples of 16 bytes.
+namespace bulk {
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ void load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ bool try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(saddr(src)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+}  // namespace bulk
+
 // Shared-memory scratch of the engine (fixed part); X follows when it fits.
 struct SmemLayout {
   int* dims;          // [n+1]
   unsigned char* flags;  // [L]
   double* red;        // [64]
+  unsigned long long* mbar;  // mbarrier of the bulk copies
   double* wn;         // [2*cap] squared column norms
   int* perm;          // [2*cap]
   double* zval;       // [n]
@@ -119,6 +150,40 @@ struct Engine {
     __syncthreads();
   }
   __device__ bool dim_ok(int d) const { return d >= 1 && d <= cap; }
+  // Bulk-copy `bytes` from global src to shared dst; every thread returns after
+  // the data has landed. The wait is bounded: on timeout the CTA records
+  // ST_COPY_TIMEOUT, waits once more (bounded) for the copy in flight, and the
+  // caller sees failed().
+  __device__ void bulk_load(void* dst, const void* src, uint32_t bytes) {
+    const uint32_t parity = (uint32_t)(sm.ibuf[13] & 1);
+    __syncthreads();
+    if (tid() == 0) {
+      bulk::fence_proxy();
+      bulk::load(dst, src, bytes, sm.mbar);
+    }
+    bool ok = false;
+    for (int it = 0; it < (1 << 22) && !ok; ++it) ok = bulk::try_wait(sm.mbar, parity);
+    const int timed_out = __syncthreads_or(!ok);
+    if (tid() == 0) sm.ibuf[13] += 1;
+    if (timed_out) {
+      bool again = false;
+      for (int it = 0; it < (1 << 22) && !again; ++it) again = bulk::try_wait(sm.mbar, parity);
+      fail(ST_COPY_TIMEOUT, (int)bytes);
+      return;
+    }
+    __syncthreads();
+  }
+  // Bulk-copy `bytes` from shared src to global dst and wait for completion.
+  __device__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+    __syncthreads();
+    if (tid() == 0) {
+      bulk::fence_proxy();
+      bulk::store(dst, src, bytes);
+      bulk::store_wait();
+      bulk::fence_proxy();
+    }
+    __syncthreads();
+  }
   __device__ __forceinline__ int tid() const { return threadIdx.x; }
   __device__ __forceinline__ int nt() const { return blockDim.x; }
 

@@ -138,6 +138,20 @@ __device__ __noinline__ void Engine<R>::cross_pass(C* XA, int na, C* XB, int nb,
   }
 }
 
+// Load of the SVD working matrix after the Jacobi: from global memory it
+// bypasses L1 (the bulk copy engine wrote it to L2 behind L1's back).
+template <typename R>
+__device__ __forceinline__ cplx<R> ld_x(const cplx<R>* p, bool in_smem) {
+  if (in_smem) return *p;
+  if constexpr (sizeof(R) == 4) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return cplx<R>{v.x, v.y};
+  } else {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return cplx<R>{v.x, v.y};
+  }
+}
+
 // Rotation parameters of a pair from its Gram entries (al = |x_p|^2,
 // be = |x_q|^2, g = x_p^H x_q = gr + i gi). Returns false when no rotation is
 // due; otherwise c, s and e^{-i phi} = (er, ei).
@@ -300,27 +314,26 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
     } else {
       C* sa = xs;
       C* sb = xs + (size_t)bw * m;
-      for (int I = 0; I < nbk; ++I) {
+      // blocks are contiguous column ranges of X: whole-block bulk copies
+      for (int I = 0; I < nbk && !failed(); ++I) {
         const int nI = min(bw, nc - I * bw);
-        const C* gI = X + (size_t)I * bw * m;
-        for (int e = tid(); e < nI * m; e += nt()) sa[e] = gI[e];
-        __syncthreads();
+        C* gI = X + (size_t)I * bw * m;
+        bulk_load(sa, gI, (uint32_t)(sizeof(C) * nI * m));
+        if (failed()) break;
         rr_pass(sa, m, nI, tol, thr);
         for (int J = I + 1; J < nbk; ++J) {
           const int nJ = min(bw, nc - J * bw);
           C* gJ = X + (size_t)J * bw * m;
-          for (int e = tid(); e < nJ * m; e += nt()) sb[e] = gJ[e];
-          __syncthreads();
+          bulk_load(sb, gJ, (uint32_t)(sizeof(C) * nJ * m));
+          if (failed()) break;
           cross(sa, nI, sb, nJ);
-          for (int e = tid(); e < nJ * m; e += nt()) gJ[e] = sb[e];
-          __syncthreads();
+          bulk_store(gJ, sb, (uint32_t)(sizeof(C) * nJ * m));
         }
-        C* gIw = X + (size_t)I * bw * m;
-        for (int e = tid(); e < nI * m; e += nt()) gIw[e] = sa[e];
-        __syncthreads();
+        bulk_store(gI, sa, (uint32_t)(sizeof(C) * nI * m));
       }
     }
     ++sweep;
+    if (failed()) break;
     const int rot = sm.ibuf[0];
     __syncthreads();
     if (rot == 0) { if (tid() == 0) sm.ibuf[1] = 1; break; }
@@ -413,10 +426,11 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
   PhaseTimer pt_trunc(st, PH_TRUNC);
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   // squared column norms (FP64 accumulation)
+  const bool x_sh = X == xs;
   for (int col = w; col < ncx; col += nw) {
     const C* x = X + (size_t)col * m;
     double s2 = 0.0;
-    for (int row = lane; row < m; row += 32) s2 += (double)abs2(x[row]);
+    for (int row = lane; row < m; row += 32) s2 += (double)abs2(ld_x(x + row, x_sh));
     s2 = warp_sum(s2);
     if (lane == 0) {
       if (!(s2 >= 0.0 && s2 <= 1.0e300)) { s2 = 0.0; sm.ibuf[14] = 1; }
@@ -489,7 +503,7 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
       const int col = sm.perm[mm];
       const double wv = sm.wn[col];
       const R inv = wv > 0.0 ? (R)(1.0 / sqrt(wv)) : R(0);
-      Ai[e] = scale(X[(size_t)col * m + row], inv);
+      Ai[e] = scale(ld_x(X + (size_t)col * m + row, x_sh), inv);
     }
     __syncthreads();
     C* Bi = S(i + 1);
@@ -512,7 +526,7 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
       const int src = sm.perm[mm];
       const double wv = sm.wn[src];
       const R inv = wv > 0.0 ? (R)(1.0 / sqrt(wv)) : R(0);
-      Bi[e] = scale(X[(size_t)src * m + col], inv);
+      Bi[e] = scale(ld_x(X + (size_t)src * m + col, x_sh), inv);
     }
     __syncthreads();
     C* Ai = S(i);
