@@ -101,6 +101,19 @@ __device__ __forceinline__ void store(void* dst, const void* src, uint32_t bytes
 __device__ __forceinline__ void store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 }  // namespace bulk
 
+// Global load that bypasses L1: for data the bulk copy engine may have
+// written behind L1's back (it also works for ordinary global data).
+template <typename R>
+__device__ __forceinline__ cplx<R> ldcg_c(const cplx<R>* p) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return cplx<R>{v.x, v.y};
+  } else {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return cplx<R>{v.x, v.y};
+  }
+}
+
 // Shared-memory scratch of the engine (fixed part); X follows when it fits.
 struct SmemLayout {
   int* dims;          // [n+1]

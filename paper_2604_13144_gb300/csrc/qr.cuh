@@ -116,10 +116,11 @@ __device__ __noinline__ void Engine<R>::qr_right() {
   }
   __syncthreads();
   qr_factor(Y, m, nq, Q, 0.0);
+  if (failed()) return;
   C* Acw = S(c);
   for (int e = tid(); e < m * r; e += nt()) {
     const int row = e / r, col = e - row * r;
-    Acw[e] = Q[(size_t)col * m + row];
+    Acw[e] = ldcg_c(Q + (size_t)col * m + row);
   }
   __syncthreads();
   const C* alpha = reinterpret_cast<const C*>(sm.hh) + 4 * cap;
@@ -129,7 +130,7 @@ __device__ __noinline__ void Engine<R>::qr_right() {
     const int ii = e / ncol, col = e - ii * ncol;
     C s = {0, 0};
     fma_c(s, alpha[ii], B[(size_t)ii * ncol + col]);
-    for (int b = ii + 1; b < nq; ++b) fma_c(s, Y[(size_t)b * m + ii], B[(size_t)b * ncol + col]);
+    for (int b = ii + 1; b < nq; ++b) fma_c(s, ldcg_c(Y + (size_t)b * m + ii), B[(size_t)b * ncol + col]);
     XG[e] = s;
   }
   __syncthreads();
@@ -156,8 +157,9 @@ __device__ __noinline__ void Engine<R>::qr_left() {
   for (int e = tid(); e < m * nq; e += nt()) { const C v = Ac[e]; Y[e] = C{v.re, -v.im}; }
   __syncthreads();
   qr_factor(Y, m, nq, Q, 0.0);
+  if (failed()) return;
   C* Acw = S(c);
-  for (int e = tid(); e < r * m; e += nt()) { const C v = Q[e]; Acw[e] = C{v.re, -v.im}; }
+  for (int e = tid(); e < r * m; e += nt()) { const C v = ldcg_c(Q + e); Acw[e] = C{v.re, -v.im}; }
   __syncthreads();
   const C* alpha = reinterpret_cast<const C*>(sm.hh) + 4 * cap;
   const int rows = 2 * d0;
@@ -169,7 +171,7 @@ __device__ __noinline__ void Engine<R>::qr_left() {
     const C* ar = Ap + (size_t)row * nq;
     fma_c(s, ar[mm], C{alpha[mm].re, -alpha[mm].im});
     for (int aa = mm + 1; aa < nq; ++aa) {
-      const C rv = Y[(size_t)aa * m + mm];
+      const C rv = ldcg_c(Y + (size_t)aa * m + mm);
       fma_c(s, ar[aa], C{rv.re, -rv.im});
     }
     XG[e] = s;
@@ -242,11 +244,9 @@ __device__ void Engine<R>::apply_block_reflector(const C* V, int m, int j0, int 
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   for (int cs = c0; cs < c1; cs += 16) {
     const int cb = min(16, c1 - cs);
-    for (int e = tid(); e < cb * m; e += nt()) {
-      const int c = e / m, row = e - c * m;
-      if (row >= j0) CH[(size_t)c * m + row] = G[(size_t)(cs + c) * m + row];
-    }
-    __syncthreads();
+    // whole columns (contiguous) by bulk copy; rows above j0 come back unchanged
+    bulk_load(CH, G + (size_t)cs * m, (uint32_t)(sizeof(C) * cb * m));
+    if (failed()) return;
     for (int e = w; e < bp * cb; e += nw) {
       const int k = e / cb, c = e - k * cb;
       const C* vk = V + (size_t)k * m;
@@ -286,9 +286,9 @@ __device__ void Engine<R>::apply_block_reflector(const C* V, int m, int j0, int 
         x.re -= vk.re * wv.re - vk.im * wv.im;
         x.im -= vk.re * wv.im + vk.im * wv.re;
       }
-      G[(size_t)(cs + c) * m + row] = x;
+      CH[(size_t)c * m + row] = x;
     }
-    __syncthreads();
+    bulk_store(G + (size_t)cs * m, CH, (uint32_t)(sizeof(C) * cb * m));
   }
 }
 
@@ -319,13 +319,10 @@ __device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq,
   C* CH = P + (size_t)m * 16;
   C* T = CH + (size_t)m * 16;
   C* Wm = T + 256;
-  for (int j0 = 0; j0 < r; j0 += 16) {
+  for (int j0 = 0; j0 < r && !failed(); j0 += 16) {
     const int bp = min(16, r - j0);
-    for (int e = tid(); e < bp * m; e += nt()) {
-      const int c = e / m, row = e - c * m;
-      if (row >= j0) P[(size_t)c * m + row] = Y[(size_t)(j0 + c) * m + row];
-    }
-    __syncthreads();
+    bulk_load(P, Y + (size_t)j0 * m, (uint32_t)(sizeof(C) * bp * m));
+    if (failed()) return;
     for (int jj = 0; jj < bp; ++jj) {
       const int j = j0 + jj;
       if (w == 0) {
@@ -372,11 +369,7 @@ __device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq,
       }
       __syncthreads();
     }
-    for (int e = tid(); e < bp * m; e += nt()) {
-      const int c = e / m, row = e - c * m;
-      if (row >= j0) Y[(size_t)(j0 + c) * m + row] = P[(size_t)c * m + row];
-    }
-    __syncthreads();
+    bulk_store(Y + (size_t)j0 * m, P, (uint32_t)(sizeof(C) * bp * m));
     if (j0 + bp < nq) {
       densify_panel(P, vhead, m, j0, bp);
       panel_t(P, m, j0, bp, T);
@@ -390,13 +383,10 @@ __device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq,
   }
   __syncthreads();
   const int last = ((r - 1) / 16) * 16;
-  for (int j0 = last; j0 >= 0; j0 -= 16) {
+  for (int j0 = last; j0 >= 0 && !failed(); j0 -= 16) {
     const int bp = min(16, r - j0);
-    for (int e = tid(); e < bp * m; e += nt()) {
-      const int c = e / m, row = e - c * m;
-      if (row >= j0) P[(size_t)c * m + row] = Y[(size_t)(j0 + c) * m + row];
-    }
-    __syncthreads();
+    bulk_load(P, Y + (size_t)j0 * m, (uint32_t)(sizeof(C) * bp * m));
+    if (failed()) return;
     densify_panel(P, vhead, m, j0, bp);
     panel_t(P, m, j0, bp, T);
     apply_block_reflector(P, m, j0, bp, T, false, Q, j0, r, CH, Wm);

@@ -395,7 +395,7 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
         for (int e = tid(); e < m * m; e += nt()) {
           const int ca = e / m, rj = e - ca * m;
           if (ca > rj) {
-            const C u = Y[(size_t)ca * m + rj];
+            const C u = y_smem ? Y[(size_t)ca * m + rj] : ldcg_c(Y + (size_t)ca * m + rj);
             X[(size_t)rj * m + ca] = C{u.re, -u.im};
             X[(size_t)ca * m + rj] = C{0, 0};
           } else if (ca == rj) {
@@ -406,7 +406,7 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
         for (int e = tid(); e < m * r; e += nt()) {
           const int j = e / m, aa = e - j * m;
           C v = {0, 0};
-          if (aa > j) { const C u = Y[(size_t)aa * nc + j]; v = C{u.re, -u.im}; }
+          if (aa > j) { const C u = ldcg_c(Y + (size_t)aa * nc + j); v = C{u.re, -u.im}; }
           else if (aa == j) v = C{alpha[j].re, -alpha[j].im};
           X[e] = v;
         }
