@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--window", type=int, default=2, help="Trotter steps evolved per sample")
-    ap.add_argument("--batch", type=int, default=0, help="samples per step (0 = 2 per SM)")
+    ap.add_argument("--batch", type=int, default=0, help="samples per step (0 = 4 per SM)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the config-1 time-to-<Z> comparison")
@@ -215,7 +215,7 @@ def run_ours(a):
     from paper_2604_13144_gb300 import tepai as T
 
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    batch = a.batch or 2 * sms
+    batch = a.batch or 4 * sms
     prob, par, init = W.bench_workload(batch, window_steps=a.window, chi=a.chi, n=a.n)
     stream = torch.cuda.current_stream()
     run = T.DeviceRun(prob, par, init, stream=stream)
@@ -241,6 +241,7 @@ def run_ours(a):
     clk = ClockSampler(local)
     t0 = time.perf_counter()
     upd, flops, kms, events, sweeps, qrm = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0
+    jpairs, jrots = 0.0, 0.0
     phases = {}
     grid = 1
     nconv, maxchi = 0, 0
@@ -252,6 +253,8 @@ def run_ours(a):
         events += st["events"]
         sweeps += st["jacobi_sweeps"]
         qrm += st["qr_moves"]
+        jpairs += st["jacobi_pairs"]
+        jrots += st["jacobi_rotations"]
         grid = st["grid_ctas"]
         for k, v in st["phase_cycles"].items():
             phases[k] = phases.get(k, 0.0) + v
@@ -315,6 +318,9 @@ def run_ours(a):
         "stats": {"events_per_s": events / elapsed, "updates": upd, "alg_flops": flops,
                   "sweeps_per_svd": sweeps / max(upd, 1.0),
                   "qr_moves_per_update": qrm / max(upd, 1.0),
+                  "jacobi_pairs_per_svd": jpairs / max(upd, 1.0),
+                  "jacobi_rotated_frac": jrots / max(jpairs, 1.0),
+                  "jacobi_cycles_per_pair": phases.get("jacobi", 0.0) / max(jpairs, 1.0),
                   "updates_per_event": upd / max(events, 1.0),
                   "phase_share": {k: round(v / max(sum(phases.values()), 1.0), 4) for k, v in phases.items()},
                   "cta_busy_frac": sum(phases.values()) / max(kms / 1e3 * SM_MAX_MHZ * 1e6 * grid, 1.0),

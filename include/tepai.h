@@ -106,14 +106,20 @@ typedef struct {
     double qr_moves;               /* orthogonality-centre moves */
     double jacobi_sweeps;          /* summed over all SVDs */
     double max_discarded_weight;
-    double alg_flops;              /* 736 chi_l chi chi_r-style algorithmic count, see DESIGN */
+    double alg_flops;              /* algorithmic real flops: 32 dl dc dr for each theta plus
+                                      4 (14 mx mn^2 + 8 mn^3) for each SVD of an mx x mn matrix */
     int max_chi;
     int n_not_converged;
-    int device_status[3];          /* first device check failure: (code, detail, CTA); code 0 = none */
+    int device_status[3];          /* first device check failure: (code, detail, CTA); code 0 =
+                                      none, 1 bond dimension out of range, 2 invalid singular-value
+                                      ranking, 3 non-finite column norm, 4 bulk copy did not land,
+                                      5 Jacobi column handoff did not arrive */
     double phase_cycles[8];        /* SM cycles per phase, summed over CTAs: init, sampler,
                                       single-site gates, theta, Jacobi SVD, truncation and
                                       write-back, centre moves (QR), measurement */
     int grid_ctas;                 /* CTAs of the ensemble launch */
+    double jacobi_pairs;           /* column pairs examined by the Jacobi sweeps */
+    double jacobi_rotations;       /* column pairs rotated by the Jacobi sweeps */
 } tepai_stats;
 
 /* Circuit event of one sample: Trotter step j (1-based), term k, setting v

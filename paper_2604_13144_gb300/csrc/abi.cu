@@ -91,39 +91,19 @@ struct Prepared {
 std::mutex g_mu;
 std::unordered_map<void*, Prepared> g_reg;
 
-struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems; };
-
 int launch_shape(const HostPlan& hp, const tepai_params* Q, int grid_req, LaunchShape& ls) {
   const NumCfg nc = num_cfg(Q->precision);
-  const int cap = Q->chi_max;
   int dev = 0;
   CK(cudaGetDevice(&dev));
   int sms = 0, optin = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  ls.block = cap >= 64 ? 512 : 256;
-  const size_t fixed = smem_fixed_bytes(hp.n, hp.L, cap, nc.csize);
-  const size_t xbytes = (size_t)4 * cap * cap * nc.csize;
-  if (fixed + xbytes <= (size_t)optin) {
-    // the whole SVD working matrix fits in shared memory
-    ls.smem = fixed + xbytes; ls.x_in_smem = 1; ls.x_elems = 4 * cap * cap;
-  } else {
-    // two staged column blocks of the working matrix: the largest power-of-two
-    // block width with 2 * bw * 2cap elements within 128 KB
-    int bw = 1;
-    while ((size_t)2 * (2 * bw) * (2 * cap) * nc.csize <= 131072 && 2 * bw < 2 * cap) bw *= 2;
-    ls.x_elems = 2 * bw * 2 * cap;
-    ls.smem = fixed + (size_t)ls.x_elems * nc.csize; ls.x_in_smem = 0;
-  }
-  if (grid_req > 0) {
-    ls.grid = grid_req;
-  } else {
-    int per_sm = 1;
-    CK(Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(ls.block, ls.smem, &per_sm)
-                                  : occupancy_ensemble_f32(ls.block, ls.smem, &per_sm));
-    if (per_sm < 1) per_sm = 1;
-    ls.grid = sms * per_sm;
-  }
+  auto occ = [&](int block, size_t smem, int* per_sm) {
+    return Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(block, smem, per_sm)
+                                      : occupancy_ensemble_f32(block, smem, per_sm);
+  };
+  CK(choose_launch_shape(hp.n, hp.L, Q->chi_max, nc.csize, optin, occ, ls));
+  ls.grid = grid_req > 0 ? grid_req : sms * ls.per_sm;
   if (Q->n_samples > 0 && ls.grid > Q->n_samples) ls.grid = (int)Q->n_samples;
   if (ls.grid < 1) ls.grid = 1;
   return TEPAI_OK;
@@ -249,6 +229,8 @@ int stats_impl(void* ws, tepai_stats* out, cudaStream_t st) {
   out->n_not_converged = (int)ds.not_converged;
   for (int p = 0; p < PH_N; ++p) out->phase_cycles[p] = (double)ds.cycles[p];
   out->grid_ctas = pr.grid;
+  out->jacobi_pairs = (double)ds.jac_pairs;
+  out->jacobi_rotations = (double)ds.jac_rots;
   return TEPAI_OK;
 }
 

@@ -71,6 +71,7 @@ struct DevStats {
   double max_discarded;
   double alg_flops;
   unsigned long long cycles[PH_N];
+  unsigned long long jac_pairs, jac_rots;  // Jacobi pair checks and rotations
 };
 
 struct KArgs {
@@ -98,7 +99,7 @@ struct KArgs {
 
 // Device status codes. A CTA that detects a broken invariant records the first
 // failure, touches no more memory for that sample, and leaves the kernel.
-enum : int { ST_OK = 0, ST_BAD_DIM = 1, ST_BAD_RANK = 2, ST_NONFINITE = 3, ST_COPY_TIMEOUT = 4 };
+enum : int { ST_OK = 0, ST_BAD_DIM = 1, ST_BAD_RANK = 2, ST_NONFINITE = 3, ST_COPY_TIMEOUT = 4, ST_HANDOFF_TIMEOUT = 5 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t al) { return (x + al - 1) / al * al; }
 

@@ -52,6 +52,7 @@ struct LocalStats {
   int max_chi = 1;
   double max_discarded = 0.0, alg_flops = 0.0;
   unsigned long long cycles[PH_N] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long jac_pairs = 0, jac_rots = 0;
 };
 
 // Adds the SM cycles of a scope to one phase counter (thread 0 only).
@@ -100,6 +101,19 @@ __device__ __forceinline__ void store(void* dst, const void* src, uint32_t bytes
 }
 __device__ __forceinline__ void store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 }  // namespace bulk
+
+// Column handoff between the warps of one CTA: a shared-memory counter per
+// column, written with release and read with acquire semantics (CTA scope).
+namespace handoff {
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(bulk::saddr(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(bulk::saddr(p)), "r"(v) : "memory");
+}
+}  // namespace handoff
 
 // Global load that bypasses L1: for data the bulk copy engine may have
 // written behind L1's back (it also works for ordinary global data).
@@ -169,9 +183,10 @@ struct Engine {
   // caller sees failed().
   __device__ void bulk_load(void* dst, const void* src, uint32_t bytes) {
     const uint32_t parity = (uint32_t)(sm.ibuf[13] & 1);
+    // every thread orders its own generic writes before the async-proxy copy
+    bulk::fence_proxy();
     __syncthreads();
     if (tid() == 0) {
-      bulk::fence_proxy();
       bulk::load(dst, src, bytes, sm.mbar);
     }
     bool ok = false;
@@ -188,14 +203,22 @@ struct Engine {
   }
   // Bulk-copy `bytes` from shared src to global dst and wait for completion.
   __device__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+    bulk::fence_proxy();
     __syncthreads();
     if (tid() == 0) {
-      bulk::fence_proxy();
       bulk::store(dst, src, bytes);
       bulk::store_wait();
       bulk::fence_proxy();
     }
     __syncthreads();
+  }
+  // Bounded wait until column counter *ver reaches r (every lane polls). A
+  // wait that runs out records ibuf[5] = 1 and returns; the pass then finishes
+  // without further waits and the caller fails the sample.
+  __device__ __forceinline__ void wait_col(const int* ver, int r) {
+    for (int it = 0; handoff::ld_acquire(ver) < r; ++it) {
+      if (it >= (1 << 22) || sm.ibuf[5]) { sm.ibuf[5] = 1; return; }
+    }
   }
   __device__ __forceinline__ int tid() const { return threadIdx.x; }
   __device__ __forceinline__ int nt() const { return blockDim.x; }

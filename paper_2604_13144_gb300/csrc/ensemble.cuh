@@ -318,6 +318,8 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
               (unsigned long long)__double_as_longlong(st.max_discarded));
     atomicAdd(&a.stats->alg_flops, st.alg_flops);
     for (int p = 0; p < PH_N; ++p) atomicAdd(&a.stats->cycles[p], st.cycles[p]);
+    atomicAdd(&a.stats->jac_pairs, st.jac_pairs);
+    atomicAdd(&a.stats->jac_rots, st.jac_rots);
   }
 }
 

@@ -211,4 +211,49 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   return TEPAI_OK;
 }
 
+// Launch shape of the ensemble kernel: threads per CTA, dynamic shared memory,
+// where the SVD working matrix lives, and resident CTAs per SM (per_sm).
+struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems, per_sm; };
+
+// Picks the shape for bond cap `cap` and complex size `csize` bytes. `occ`
+// reports resident CTAs per SM of a (block, smem) pair. When the whole SVD
+// working matrix (2cap x 2cap) fits in shared memory it stays there; otherwise
+// it lives in global memory and column blocks are staged. Staged shapes first
+// try two samples per SM (256 threads each, staging room for one 32-column
+// Householder panel pair, which also holds two 16-column Jacobi blocks): two
+// independent CTAs fill each other's barrier and latency stalls. If two do
+// not fit, one 512-thread CTA per SM stages blocks within 128 KB.
+template <class Occ>
+inline cudaError_t choose_launch_shape(int n, int L, int cap, int csize, int optin, Occ occ, LaunchShape& ls) {
+  const size_t fixed = smem_fixed_bytes(n, L, cap, csize);
+  const size_t xbytes = (size_t)4 * cap * cap * csize;
+  int per_sm = 1;
+  cudaError_t e;
+  if (fixed + xbytes <= (size_t)optin) {
+    ls.block = cap >= 64 ? 512 : 256;
+    ls.x_in_smem = 1;
+    ls.x_elems = 4 * cap * cap;
+    ls.smem = fixed + xbytes;
+    e = occ(ls.block, ls.smem, &per_sm);
+  } else {
+    ls.block = 256;
+    ls.x_in_smem = 0;
+    ls.x_elems = 2 * cap * 36 > 2 * cap * 32 + 512 ? 2 * cap * 36 : 2 * cap * 32 + 512;
+    ls.smem = fixed + (size_t)ls.x_elems * csize;
+    e = ls.smem <= (size_t)optin ? occ(ls.block, ls.smem, &per_sm) : cudaSuccess;
+    if (e != cudaSuccess) return e;
+    if (ls.smem > (size_t)optin || per_sm < 2) {
+      int bw = 1;
+      while ((size_t)2 * (2 * bw) * (2 * cap) * csize <= 131072 && 2 * bw < 2 * cap) bw *= 2;
+      ls.block = 512;
+      ls.x_elems = 2 * bw * 2 * cap;
+      ls.smem = fixed + (size_t)ls.x_elems * csize;
+      per_sm = 1;
+      e = occ(ls.block, ls.smem, &per_sm);
+    }
+  }
+  ls.per_sm = per_sm < 1 ? 1 : per_sm;
+  return e;
+}
+
 }  // namespace tepai

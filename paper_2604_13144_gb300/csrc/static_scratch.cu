@@ -81,28 +81,20 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
   const size_t o_arena = o;
   const size_t stride = a256(((size_t)hp.n * 2 * cap * cap + 8 * (size_t)cap * cap) * csize);
   if (o_arena + stride > kStaticScratchBytes) return TEPAI_ERR_WORKSPACE_TOO_SMALL;
-  // launch shape: the working matrix in shared memory when it fits, else two
-  // staged column blocks (the same rule as the allocating entry points)
+  // launch shape: the same rule as the allocating entry points
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return TEPAI_ERR_CUDA;
-  const int block = cap >= 64 ? 512 : 256;
-  const size_t fixed = smem_fixed_bytes(hp.n, hp.L, cap, csize);
-  size_t smem;
-  int x_elems, x_in_smem;
-  if (fixed + (size_t)4 * cap * cap * csize <= (size_t)optin) {
-    x_elems = 4 * cap * cap; x_in_smem = 1; smem = fixed + (size_t)x_elems * csize;
-  } else {
-    int bw = 1;
-    while ((size_t)2 * (2 * bw) * (2 * cap) * csize <= 131072 && 2 * bw < 2 * cap) bw *= 2;
-    x_elems = 2 * bw * 2 * cap; x_in_smem = 0; smem = fixed + (size_t)x_elems * csize;
-  }
-  int per_sm = 1;
-  if ((Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(block, smem, &per_sm)
-                                  : occupancy_ensemble_f32(block, smem, &per_sm)) != cudaSuccess)
-    return TEPAI_ERR_CUDA;
+  auto occ = [&](int blk, size_t sm_bytes, int* per) {
+    return Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(blk, sm_bytes, per)
+                                      : occupancy_ensemble_f32(blk, sm_bytes, per);
+  };
+  LaunchShape ls{};
+  if (choose_launch_shape(hp.n, hp.L, cap, csize, optin, occ, ls) != cudaSuccess) return TEPAI_ERR_CUDA;
+  const int block = ls.block, x_elems = ls.x_elems, x_in_smem = ls.x_in_smem, per_sm = ls.per_sm;
+  const size_t smem = ls.smem;
   long long grid = (long long)sms * (per_sm < 1 ? 1 : per_sm);
   const long long fit = (long long)((kStaticScratchBytes - o_arena) / stride);
   if (grid > fit) grid = fit;

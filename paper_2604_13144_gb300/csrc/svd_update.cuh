@@ -48,6 +48,113 @@ __device__ __noinline__ void Engine<R>::form_theta(int i, const C g[16], bool en
   __syncthreads();
 }
 
+// Warp sums of several scalars at once by a transposing butterfly: each xor
+// level halves the number of values a lane carries (it keeps one half and
+// sends the other to its partner), so 4 values take 2 + 1 shuffles and 8 take
+// 4 + 2 + 1 before the last levels reduce the single survivor. Every lane ends
+// with the totals, read from one lane each, so all lanes hold bit-identical
+// sums and take the same branch on them.
+template <typename R>
+__device__ __forceinline__ void warp_sum4(R v[4], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8;
+  R w[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const R send = b4 ? v[j] : v[j + 2], keep = b4 ? v[j + 2] : v[j];
+    w[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  // w[j] carries value j + 2*b4
+  R z;
+  {
+    const R send = b3 ? w[0] : w[1], keep = b3 ? w[1] : w[0];
+    z = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  // z carries value b3 + 2*b4, summed over lanes that differ in bits 4 and 3
+  z += __shfl_xor_sync(0xffffffffu, z, 4);
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = __shfl_sync(0xffffffffu, z, 8 * j);
+}
+
+template <typename R>
+__device__ __forceinline__ void warp_sum8(R v[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  R w[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const R send = b4 ? v[j] : v[j + 4], keep = b4 ? v[j + 4] : v[j];
+    w[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  // w[j] carries value j + 4*b4
+  R u[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const R send = b3 ? w[j] : w[j + 2], keep = b3 ? w[j + 2] : w[j];
+    u[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  // u[j] carries value j + 2*b3 + 4*b4
+  R z;
+  {
+    const R send = b2 ? u[0] : u[1], keep = b2 ? u[1] : u[0];
+    z = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  // z carries value b2 + 2*b3 + 4*b4, summed over lanes that differ in bits 4..2
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __shfl_sync(0xffffffffu, z, 4 * j);
+}
+
+// Rotation parameters of a pair from its Gram entries (al = |x_p|^2,
+// be = |x_q|^2, g = x_p^H x_q = gr + i gi). Returns false when no rotation is
+// due; otherwise c, s and e^{-i phi} = (er, ei). The angle follows the
+// classical Jacobi formulas: zeta = (be - al) / (2|g|), t = sign(zeta) /
+// (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t.
+template <typename R>
+__device__ __forceinline__ bool rot_params(R al, R be, R gr, R gi, R tol, R thr, R& c, R& s, R& er, R& ei) {
+  if (al < thr || be < thr) return false;
+  if constexpr (sizeof(R) == 4) {
+    // Single precision: 1/|g| from one reciprocal square root serves the
+    // rotation test, zeta and the phase, so the dependent chain between the
+    // warp sums and the rotation holds no division and no square root. The
+    // phase has unit modulus and c^2 + s^2 = 1 to rsqrt accuracy (a few ulp).
+    // A zero or non-finite g gives NaN in the test and no rotation.
+    const float h = fmaf(gr, gr, gi * gi);
+    const float ig = rsqrtf(h);
+    const float cosv = (h * ig) * (rsqrtf(al) * rsqrtf(be));
+    if (!(cosv > tol)) return false;
+    const float zeta = 0.5f * (be - al) * ig;
+    const float az = fabsf(zeta);
+    float tt;
+    if (az < 1.0e15f) {
+      const float q = fmaf(az, az, 1.0f);
+      tt = __fdividef(1.0f, az + q * rsqrtf(q));
+    } else {
+      tt = __fdividef(0.5f, az);
+    }
+    if (zeta < 0.0f) tt = -tt;
+    c = rsqrtf(fmaf(tt, tt, 1.0f));
+    s = c * tt;
+    er = gr * ig;
+    ei = -gi * ig;
+    return true;
+  } else {
+    const R g = sqrt(gr * gr + gi * gi);
+    if (!(g > tol * sqrt(al * be))) return false;
+    const R zeta = (be - al) / (R(2) * g);
+    const R az = fabs(zeta);
+    R tt = az > R(1) ? R(1) / (az * (R(1) + sqrt(R(1) + R(1) / (az * az))))
+                     : R(1) / (az + sqrt(R(1) + az * az));
+    if (zeta < R(0)) tt = -tt;
+    c = rsqrt_<R>(R(1) + tt * tt);
+    s = c * tt;
+    er = gr / g;
+    ei = -gi / g;
+    return true;
+  }
+}
+
 // One Jacobi rotation of the column pair (xp, xq), by one warp: the pair is
 // rotated when |x_p^H x_q| > tol |x_p||x_q| and neither column is below thr
 // (zero to working precision). The complex rotation first removes the phase
@@ -70,17 +177,13 @@ __device__ __forceinline__ bool rotate_pair(cplx<R>* xp, cplx<R>* xq, int m, R t
     gr = fma(u[t].re, v[t].re, fma(u[t].im, v[t].im, gr));
     gi = fma(u[t].re, v[t].im, fma(-u[t].im, v[t].re, gi));
   }
-  al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
-  if (al < thr || be < thr) return false;
-  const R g = sqrt(gr * gr + gi * gi);
-  if (!(g > tol * sqrt(al * be))) return false;
-  const R zeta = (be - al) / (R(2) * g);
-  const R az = fabs(zeta);
-  R tt = az > R(1) ? R(1) / (az * (R(1) + sqrt(R(1) + R(1) / (az * az))))
-                   : R(1) / (az + sqrt(R(1) + az * az));
-  if (zeta < R(0)) tt = -tt;
-  const R c = rsqrt_<R>(R(1) + tt * tt), s = c * tt;
-  const R er = gr / g, ei = -gi / g;  // e^{-i phi}
+  {
+    R v4[4] = {al, be, gr, gi};
+    warp_sum4<R>(v4, lane);
+    al = v4[0]; be = v4[1]; gr = v4[2]; gi = v4[3];
+  }
+  R c, s, er, ei;
+  if (!rot_params<R>(al, be, gr, gi, tol, thr, c, s, er, ei)) return false;
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     const int row = lane + 32 * t;
@@ -103,23 +206,42 @@ __device__ __forceinline__ bool rotate_pair_m(cplx<R>* xp, cplx<R>* xq, int m, R
 
 // One cyclic pass over all pairs of the nc columns of X (m rows, column-major)
 // in parallel round-robin order (Brent & Luk, SIAM J. Sci. Stat. Comput. 6,
-// 1985): nc-1 rounds of disjoint pairs, one warp per pair. Rotations are
+// 1985): np-1 rounds of disjoint pairs (np = nc rounded up to even), slot t
+// of every round owned by warp t mod nw. Rounds are not separated by CTA
+// barriers: every column is touched by exactly one slot per round, and a slot
+// waits only until both of its columns have finished the previous round
+// (counter ver[c] = rounds completed on column c, in sm.perm). Warps therefore
+// drift apart and overlap their latency-bound phases, while every pair sees
+// exactly the column values of the barrier-separated schedule. Rotations are
 // counted in ibuf[0].
 template <typename R>
 __device__ __noinline__ void Engine<R>::rr_pass(C* X, int m, int nc, R tol, R thr) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int np = nc + (nc & 1);
+  int* ver = sm.perm;
+  for (int c = tid(); c < np; c += nt()) ver[c] = 0;
+  __syncthreads();
+  int rot = 0, chk = 0;
   for (int r = 0; r < np - 1; ++r) {
     for (int t = w; t < np / 2; t += nw) {
       int p, q;
       if (t == 0) { p = np - 1; q = r; }
       else { p = (r + t) % (np - 1); q = (r - t + np - 1) % (np - 1); }
-      if (p >= nc || q >= nc) continue;
-      if (rotate_pair_m<R>(X + (size_t)p * m, X + (size_t)q * m, m, tol, thr, lane) && lane == 0)
-        atomicAdd(&sm.ibuf[0], 1);
+      wait_col(ver + p, r);
+      wait_col(ver + q, r);
+      if (p < nc && q < nc) {
+        ++chk;
+        if (rotate_pair_m<R>(X + (size_t)p * m, X + (size_t)q * m, m, tol, thr, lane)) ++rot;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        handoff::st_release(ver + p, r + 1);
+        handoff::st_release(ver + q, r + 1);
+      }
     }
-    __syncthreads();
   }
+  if (lane == 0) { if (rot) atomicAdd(&sm.ibuf[0], rot); if (chk) atomicAdd(&sm.ibuf[6], chk); }
+  __syncthreads();
 }
 
 // All pairs (p in block A, q in block B): round r pairs p with (p + r) mod nmax.
@@ -131,6 +253,7 @@ __device__ __noinline__ void Engine<R>::cross_pass(C* XA, int na, C* XB, int nb,
     for (int p = w; p < nmax; p += nw) {
       const int q = (p + r) % nmax;
       if (p >= na || q >= nb) continue;
+      if (lane == 0) atomicAdd(&sm.ibuf[6], 1);
       if (rotate_pair_m<R>(XA + (size_t)p * m, XB + (size_t)q * m, m, tol, thr, lane) && lane == 0)
         atomicAdd(&sm.ibuf[0], 1);
     }
@@ -152,36 +275,23 @@ __device__ __forceinline__ cplx<R> ld_x(const cplx<R>* p, bool in_smem) {
   }
 }
 
-// Rotation parameters of a pair from its Gram entries (al = |x_p|^2,
-// be = |x_q|^2, g = x_p^H x_q = gr + i gi). Returns false when no rotation is
-// due; otherwise c, s and e^{-i phi} = (er, ei).
-template <typename R>
-__device__ __forceinline__ bool rot_params(R al, R be, R gr, R gi, R tol, R thr, R& c, R& s, R& er, R& ei) {
-  if (al < thr || be < thr) return false;
-  const R g = sqrt(gr * gr + gi * gi);
-  if (!(g > tol * sqrt(al * be))) return false;
-  const R zeta = (be - al) / (R(2) * g);
-  const R az = fabs(zeta);
-  R tt = az > R(1) ? R(1) / (az * (R(1) + sqrt(R(1) + R(1) / (az * az))))
-                   : R(1) / (az + sqrt(R(1) + az * az));
-  if (zeta < R(0)) tt = -tt;
-  c = rsqrt_<R>(R(1) + tt * tt);
-  s = c * tt;
-  er = gr / g;
-  ei = -gi / g;
-  return true;
-}
-
 // Cross pairs of blocks A and B (na, nb <= 2 * warps) with the warp-owned A
-// columns held in registers: warp w owns A columns w and w + nw for the whole
-// pass; in round r they meet B columns (p + r) mod nmax. Only B columns move
+// columns held in registers: warp w owns A slots w and w + nw for the whole
+// pass; in round r slot p meets B column (p + r) mod nmax. Only B columns move
 // through shared memory, and the two pairs of a warp are processed together.
+// As in rr_pass, rounds are ordered per column instead of by CTA barriers: B
+// column q is touched by one slot per round, and the slot waits until q has
+// finished the previous round (ver[q], in sm.perm).
 template <typename R>
 template <int RPL>
 __device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int nmax = max(na, nb);
+  int* ver = sm.perm;
+  for (int c = tid(); c < nmax; c += nt()) ver[c] = 0;
+  __syncthreads();
   const int p0 = w, p1 = w + nw;
+  const bool o0 = p0 < nmax, o1 = p1 < nmax;  // slots this warp owns
   const bool h0 = p0 < na, h1 = p1 < na;
   C a0[RPL], a1[RPL], b0[RPL], b1[RPL];
 #pragma unroll
@@ -190,10 +300,13 @@ __device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, in
     a0[t] = (h0 && row < m) ? XA[(size_t)p0 * m + row] : C{0, 0};
     a1[t] = (h1 && row < m) ? XA[(size_t)p1 * m + row] : C{0, 0};
   }
-  int rot = 0;
-  for (int r = 0; r < nmax; ++r) {
+  int rot = 0, chk = 0;
+  for (int r = 0; r < nmax && o0; ++r) {
     const int q0 = (p0 + r) % nmax, q1 = (p1 + r) % nmax;
+    wait_col(ver + q0, r);
+    if (o1) wait_col(ver + q1, r);
     const bool d0 = h0 && q0 < nb, d1 = h1 && q1 < nb;
+    chk += (int)d0 + (int)d1;
     C* xb0 = XB + (size_t)q0 * m;
     C* xb1 = XB + (size_t)q1 * m;
     R al0 = 0, be0 = 0, gr0 = 0, gi0 = 0, al1 = 0, be1 = 0, gr1 = 0, gi1 = 0;
@@ -211,12 +324,11 @@ __device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, in
       gr1 = fma(a1[t].re, b1[t].re, fma(a1[t].im, b1[t].im, gr1));
       gi1 = fma(a1[t].re, b1[t].im, fma(-a1[t].im, b1[t].re, gi1));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      al0 += __shfl_xor_sync(0xffffffffu, al0, o); be0 += __shfl_xor_sync(0xffffffffu, be0, o);
-      gr0 += __shfl_xor_sync(0xffffffffu, gr0, o); gi0 += __shfl_xor_sync(0xffffffffu, gi0, o);
-      al1 += __shfl_xor_sync(0xffffffffu, al1, o); be1 += __shfl_xor_sync(0xffffffffu, be1, o);
-      gr1 += __shfl_xor_sync(0xffffffffu, gr1, o); gi1 += __shfl_xor_sync(0xffffffffu, gi1, o);
+    {
+      R v8[8] = {al0, be0, gr0, gi0, al1, be1, gr1, gi1};
+      warp_sum8<R>(v8, lane);
+      al0 = v8[0]; be0 = v8[1]; gr0 = v8[2]; gi0 = v8[3];
+      al1 = v8[4]; be1 = v8[5]; gr1 = v8[6]; gi1 = v8[7];
     }
     R c0, s0, er0, ei0, c1, s1, er1, ei1;
     const bool r0 = d0 && rot_params<R>(al0, be0, gr0, gi0, tol, thr, c0, s0, er0, ei0);
@@ -245,7 +357,11 @@ __device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, in
       }
       ++rot;
     }
-    __syncthreads();
+    __syncwarp();
+    if (lane == 0) {
+      handoff::st_release(ver + q0, r + 1);
+      if (o1) handoff::st_release(ver + q1, r + 1);
+    }
   }
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
@@ -255,7 +371,7 @@ __device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, in
       if (h1) XA[(size_t)p1 * m + row] = a1[t];
     }
   }
-  if (lane == 0 && rot) atomicAdd(&sm.ibuf[0], rot);
+  if (lane == 0) { if (rot) atomicAdd(&sm.ibuf[0], rot); if (chk) atomicAdd(&sm.ibuf[6], chk); }
   __syncthreads();
 }
 
@@ -273,18 +389,64 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
   // rounding noise of a length-m dot product grows like sqrt(m) eps, so a fixed
   // tolerance would leave the last sweeps rotating pairs on noise alone
   const R tol = (R)(a.tol * sqrt((double)m));
+  const int lane = tid() & 31, nw = nt() >> 5;
+  // squared column norms (FP64 accumulation) and ||X||_F^2
+  for (int col = tid() >> 5; col < nc; col += nw) {
+    const C* x = X + (size_t)col * m;
+    double s2 = 0.0;
+    for (int row = lane; row < m; row += 32) s2 += (double)abs2(ld_x(x + row, x_in_smem));
+    s2 = warp_sum(s2);
+    if (lane == 0) sm.wn[col] = s2;
+  }
+  __syncthreads();
+  double fro = 0.0;
+  for (int col = tid(); col < nc; col += nt()) fro += sm.wn[col];
+  fro = block_sum(fro, sm.red);
   // columns below floor_rel/4 of the matrix norm are zero to working precision
   // (they will be discarded): they are not rotated, so that the nc - m null
   // columns of a wide matrix settle instead of shrinking towards underflow
-  double fro = 0.0;
-  for (int e = tid(); e < m * nc; e += nt()) fro += (double)abs2(X[e]);
-  fro = block_sum(fro, sm.red);
   const R thr = (R)(0.0625 * a.floor_rel * a.floor_rel * fro);
+  // A pair is rotated only when both of its columns are at or above thr, so a
+  // column that starts below thr keeps its values through every sweep. Those
+  // columns are swapped behind the active ones and the sweeps visit only the
+  // active prefix: a two-site theta of rank ~chi plus a small gate term has
+  // about half of its R^H columns below thr, and skipping them removes most
+  // of the pair checks of a sweep without changing any rotation's arithmetic.
+  if (tid() == 0) {
+    const double thr_d = (double)thr;
+    int na = 0;
+    for (int j = 0; j < nc; ++j) na += sm.wn[j] >= thr_d;
+    int ns = 0, q = na;
+    for (int j = 0; j < na; ++j) {
+      if (sm.wn[j] >= thr_d) continue;
+      while (q < nc && sm.wn[q] < thr_d) ++q;
+      if (q >= nc) break;  // unreachable: the counts of the two sides agree
+      sm.perm[2 * ns] = j;
+      sm.perm[2 * ns + 1] = q;
+      ++ns;
+      ++q;
+    }
+    sm.ibuf[3] = na;
+    sm.ibuf[4] = ns;
+    sm.ibuf[1] = 0;
+    sm.ibuf[5] = 0;  // column handoff timeout flag of the passes
+  }
+  __syncthreads();
+  const int n_act = sm.ibuf[3], n_swap = sm.ibuf[4];
+  for (int sidx = tid() >> 5; sidx < n_swap; sidx += nw) {
+    C* xp = X + (size_t)sm.perm[2 * sidx] * m;
+    C* xq = X + (size_t)sm.perm[2 * sidx + 1] * m;
+    for (int row = lane; row < m; row += 32) {
+      const C u = ld_x(xp + row, x_in_smem), v = ld_x(xq + row, x_in_smem);
+      xp[row] = v;
+      xq[row] = u;
+    }
+  }
+  __syncthreads();
+  nc = n_act;
   int sweep = 0;
-  if (tid() == 0) sm.ibuf[1] = 0;
   if (nc < 2) { __syncthreads(); if (tid() == 0) sm.ibuf[1] = 1; __syncthreads(); return 0; }
   C* xs = reinterpret_cast<C*>(sm.x);
-  const int nw = nt() >> 5;
   // column blocks of bw: the width the staging buffer allows, at most 2 columns
   // per warp so that a block's warp-owned columns fit in registers
   int bw = 1;
@@ -302,7 +464,7 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
     else cross_pass(XA, na, XB, nbb, m, tol, thr);
   };
   while (sweep < a.max_sweeps) {
-    if (tid() == 0) sm.ibuf[0] = 0;
+    if (tid() == 0) { sm.ibuf[0] = 0; sm.ibuf[6] = 0; }
     __syncthreads();
     if (x_in_smem) {
       for (int I = 0; I < nbk; ++I) {
@@ -334,7 +496,9 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
     }
     ++sweep;
     if (failed()) break;
+    if (sm.ibuf[5]) { fail(ST_HANDOFF_TIMEOUT, sweep); break; }
     const int rot = sm.ibuf[0];
+    if (tid() == 0) { st.jac_rots += (unsigned long long)rot; st.jac_pairs += (unsigned long long)sm.ibuf[6]; }
     __syncthreads();
     if (rot == 0) { if (tid() == 0) sm.ibuf[1] = 1; break; }
   }

@@ -58,7 +58,8 @@ class Stats(C.Structure):
                 ("max_discarded_weight", C.c_double), ("alg_flops", C.c_double),
                 ("max_chi", C.c_int), ("n_not_converged", C.c_int),
                 ("device_status", C.c_int * 3), ("phase_cycles", C.c_double * 8),
-                ("grid_ctas", C.c_int)]
+                ("grid_ctas", C.c_int), ("jacobi_pairs", C.c_double),
+                ("jacobi_rotations", C.c_double)]
 
     PHASES = ("init", "sampler", "single_site", "theta", "jacobi", "truncate", "qr", "measure")
 
