@@ -242,7 +242,7 @@ def run_ours(a):
     t0 = time.perf_counter()
     upd, flops, kms, events, sweeps, qrm = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0
     jpairs, jrots = 0.0, 0.0
-    phases = {}
+    phases, subphases = {}, {}
     grid = 1
     nconv, maxchi = 0, 0
     for i in range(a.steps):
@@ -258,6 +258,8 @@ def run_ours(a):
         grid = st["grid_ctas"]
         for k, v in st["phase_cycles"].items():
             phases[k] = phases.get(k, 0.0) + v
+        for k, v in st["subphase_cycles"].items():
+            subphases[k] = subphases.get(k, 0.0) + v
         nconv += st["n_not_converged"]
         maxchi = max(maxchi, st["max_chi"])
     torch.cuda.synchronize()
@@ -323,6 +325,8 @@ def run_ours(a):
                   "jacobi_cycles_per_pair": phases.get("jacobi", 0.0) / max(jpairs, 1.0),
                   "updates_per_event": upd / max(events, 1.0),
                   "phase_share": {k: round(v / max(sum(phases.values()), 1.0), 4) for k, v in phases.items()},
+                  "subphase_share": {k: round(v / max(sum(phases.values()), 1.0), 4)
+                                     for k, v in subphases.items()},
                   "cta_busy_frac": sum(phases.values()) / max(kms / 1e3 * SM_MAX_MHZ * 1e6 * grid, 1.0),
                   "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi},
     }

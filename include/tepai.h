@@ -120,6 +120,10 @@ typedef struct {
     int grid_ctas;                 /* CTAs of the ensemble launch */
     double jacobi_pairs;           /* column pairs examined by the Jacobi sweeps */
     double jacobi_rotations;       /* column pairs rotated by the Jacobi sweeps */
+    double subphase_cycles[8];     /* SM cycles of parts nested in the phases above: Householder
+                                      panels, trailing block-reflector updates, explicit Q, R times
+                                      the neighbour site, SVD projection and write-back, waits on
+                                      bulk copies, Jacobi passes, singular-value ranking */
 } tepai_stats;
 
 /* Circuit event of one sample: Trotter step j (1-based), term k, setting v

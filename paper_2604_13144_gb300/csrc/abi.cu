@@ -231,6 +231,7 @@ int stats_impl(void* ws, tepai_stats* out, cudaStream_t st) {
   out->grid_ctas = pr.grid;
   out->jacobi_pairs = (double)ds.jac_pairs;
   out->jacobi_rotations = (double)ds.jac_rots;
+  for (int p = 0; p < SP_N; ++p) out->subphase_cycles[p] = (double)ds.sub_cycles[p];
   return TEPAI_OK;
 }
 

@@ -64,6 +64,11 @@ struct TermDev {
 
 // Phases timed with clock64 by thread 0 of every CTA (SM cycles, summed over CTAs).
 enum : int { PH_INIT = 0, PH_SAMPLER, PH_SINGLE, PH_THETA, PH_JACOBI, PH_TRUNC, PH_QR, PH_MEASURE, PH_N };
+// Sub-phases, nested inside the phases above (counted separately): Householder
+// panel factorisation, trailing block-reflector updates, explicit Q, R times
+// the neighbour site, SVD projection and write-back, waits on bulk copies,
+// Jacobi passes, singular-value ranking and truncation bookkeeping.
+enum : int { SP_QR_PANEL = 0, SP_QR_APPLY, SP_QR_FORMQ, SP_QR_RMUL, SP_PROJ, SP_BULK, SP_PASSES, SP_RANK, SP_N };
 
 struct DevStats {
   unsigned long long events, gate_updates, swap_updates, qr_moves, sweeps, not_converged;
@@ -72,6 +77,7 @@ struct DevStats {
   double alg_flops;
   unsigned long long cycles[PH_N];
   unsigned long long jac_pairs, jac_rots;  // Jacobi pair checks and rotations
+  unsigned long long sub_cycles[SP_N];
 };
 
 struct KArgs {

@@ -11,6 +11,7 @@
 // Every member function is called by all threads of the CTA with uniform
 // arguments; they synchronise internally.
 #pragma once
+#include "gemm.cuh"
 #include "common.cuh"
 
 namespace tepai {
@@ -53,9 +54,28 @@ struct LocalStats {
   double max_discarded = 0.0, alg_flops = 0.0;
   unsigned long long cycles[PH_N] = {0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long jac_pairs = 0, jac_rots = 0;
+  unsigned long long sub_cycles[SP_N] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 // Adds the SM cycles of a scope to one phase counter (thread 0 only).
+struct SubTimer {
+  LocalStats& st;
+  int sp;
+  long long t0 = 0;
+  __device__ SubTimer(LocalStats& s, int p) : st(s), sp(p) {
+#ifdef __CUDA_ARCH__
+    if (threadIdx.x == 0) t0 = clock64();
+#endif
+  }
+  __device__ void stop() {
+#ifdef __CUDA_ARCH__
+    if (threadIdx.x == 0 && sp >= 0) st.sub_cycles[sp] += (unsigned long long)(clock64() - t0);
+#endif
+    sp = -1;
+  }
+  __device__ ~SubTimer() { stop(); }
+};
+
 struct PhaseTimer {
   LocalStats& st;
   int ph;
@@ -182,6 +202,7 @@ struct Engine {
   // ST_COPY_TIMEOUT, waits once more (bounded) for the copy in flight, and the
   // caller sees failed().
   __device__ void bulk_load(void* dst, const void* src, uint32_t bytes) {
+    SubTimer sbt(st, SP_BULK);
     const uint32_t parity = (uint32_t)(sm.ibuf[13] & 1);
     // every thread orders its own generic writes before the async-proxy copy
     bulk::fence_proxy();
@@ -203,6 +224,7 @@ struct Engine {
   }
   // Bulk-copy `bytes` from shared src to global dst and wait for completion.
   __device__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+    SubTimer sbt(st, SP_BULK);
     bulk::fence_proxy();
     __syncthreads();
     if (tid() == 0) {

@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
     for (int p = 0; p < PH_N; ++p) atomicAdd(&a.stats->cycles[p], st.cycles[p]);
     atomicAdd(&a.stats->jac_pairs, st.jac_pairs);
     atomicAdd(&a.stats->jac_rots, st.jac_rots);
+    for (int p = 0; p < SP_N; ++p) atomicAdd(&a.stats->sub_cycles[p], st.sub_cycles[p]);
   }
 }
 

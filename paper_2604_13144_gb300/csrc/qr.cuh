@@ -21,6 +21,8 @@ __device__ __noinline__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, d
   C* vhead = reinterpret_cast<C*>(sm.hh);
   C* tau = vhead + 2 * cap;
   C* alpha = tau + 2 * cap;
+  {
+  SubTimer spt(st, SP_QR_PANEL);
   for (int j = 0; j < r; ++j) {
     if (w == 0) {
       const C* y = Y + (size_t)j * m;
@@ -66,7 +68,9 @@ __device__ __noinline__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, d
     }
     __syncthreads();
   }
+  }
   if (Q == nullptr) return;
+  SubTimer sqt(st, SP_QR_FORMQ);
   for (int e = tid(); e < m * r; e += nt()) {
     const int col = e / m, row = e - col * m;
     Q[e] = C{row == col ? R(1) : R(0), 0};
@@ -117,6 +121,7 @@ __device__ __noinline__ void Engine<R>::qr_right() {
   __syncthreads();
   qr_factor(Y, m, nq, Q, 0.0);
   if (failed()) return;
+  SubTimer smt(st, SP_QR_RMUL);
   C* Acw = S(c);
   for (int e = tid(); e < m * r; e += nt()) {
     const int row = e / r, col = e - row * r;
@@ -126,12 +131,24 @@ __device__ __noinline__ void Engine<R>::qr_right() {
   const C* alpha = reinterpret_cast<const C*>(sm.hh) + 4 * cap;
   const int ncol = 2 * d2;
   const C* B = S(c + 1);
-  for (int e = tid(); e < r * ncol; e += nt()) {
-    const int ii = e / ncol, col = e - ii * ncol;
-    C s = {0, 0};
-    fma_c(s, alpha[ii], B[(size_t)ii * ncol + col]);
-    for (int b = ii + 1; b < nq; ++b) fma_c(s, ldcg_c(Y + (size_t)b * m + ii), B[(size_t)b * ncol + col]);
-    XG[e] = s;
+  C* out = XG;
+  if (a.smem_x_elems >= gemm_tile_elems(nt())) {
+    // R (upper triangle in Y above the diagonal, diagonal in alpha) times A_{c+1}
+    const C* yp = Y;
+    block_gemm<R>(r, ncol, nq, reinterpret_cast<C*>(sm.x),
+        [=](int ii, int kk) {
+          return kk < ii ? C{0, 0} : (kk == ii ? alpha[ii] : ldcg_c(yp + (size_t)kk * m + ii));
+        },
+        [=](int kk, int jj) { return B[(size_t)kk * ncol + jj]; },
+        [=](int ii, int jj, C v) { out[(size_t)ii * ncol + jj] = v; });
+  } else {
+    for (int e = tid(); e < r * ncol; e += nt()) {
+      const int ii = e / ncol, col = e - ii * ncol;
+      C s = {0, 0};
+      fma_c(s, alpha[ii], B[(size_t)ii * ncol + col]);
+      for (int b = ii + 1; b < nq; ++b) fma_c(s, ldcg_c(Y + (size_t)b * m + ii), B[(size_t)b * ncol + col]);
+      XG[e] = s;
+    }
   }
   __syncthreads();
   C* Bw = S(c + 1);
@@ -158,23 +175,38 @@ __device__ __noinline__ void Engine<R>::qr_left() {
   __syncthreads();
   qr_factor(Y, m, nq, Q, 0.0);
   if (failed()) return;
+  SubTimer smt(st, SP_QR_RMUL);
   C* Acw = S(c);
   for (int e = tid(); e < r * m; e += nt()) { const C v = ldcg_c(Q + e); Acw[e] = C{v.re, -v.im}; }
   __syncthreads();
   const C* alpha = reinterpret_cast<const C*>(sm.hh) + 4 * cap;
   const int rows = 2 * d0;
   const C* Ap = S(c - 1);
-  for (int e = tid(); e < rows * r; e += nt()) {
-    const int row = e / r, mm = e - row * r;
-    // out[row][mm] = sum_{a >= mm} A[row][a] conj(R[mm][a])
-    C s = {0, 0};
-    const C* ar = Ap + (size_t)row * nq;
-    fma_c(s, ar[mm], C{alpha[mm].re, -alpha[mm].im});
-    for (int aa = mm + 1; aa < nq; ++aa) {
-      const C rv = ldcg_c(Y + (size_t)aa * m + mm);
-      fma_c(s, ar[aa], C{rv.re, -rv.im});
+  C* out = XG;
+  if (a.smem_x_elems >= gemm_tile_elems(nt())) {
+    // A_{c-1} times R^H (R: upper triangle in Y above the diagonal, diagonal in alpha)
+    const C* yp = Y;
+    block_gemm<R>(rows, r, nq, reinterpret_cast<C*>(sm.x),
+        [=](int ii, int kk) { return Ap[(size_t)ii * nq + kk]; },
+        [=](int kk, int jj) {
+          if (kk < jj) return C{0, 0};
+          const C u = kk == jj ? alpha[jj] : ldcg_c(yp + (size_t)kk * m + jj);
+          return C{u.re, -u.im};
+        },
+        [=](int ii, int jj, C v) { out[(size_t)ii * r + jj] = v; });
+  } else {
+    for (int e = tid(); e < rows * r; e += nt()) {
+      const int row = e / r, mm = e - row * r;
+      // out[row][mm] = sum_{a >= mm} A[row][a] conj(R[mm][a])
+      C s = {0, 0};
+      const C* ar = Ap + (size_t)row * nq;
+      fma_c(s, ar[mm], C{alpha[mm].re, -alpha[mm].im});
+      for (int aa = mm + 1; aa < nq; ++aa) {
+        const C rv = ldcg_c(Y + (size_t)aa * m + mm);
+        fma_c(s, ar[aa], C{rv.re, -rv.im});
+      }
+      XG[e] = s;
     }
-    XG[e] = s;
   }
   __syncthreads();
   C* Apw = S(c - 1);
@@ -321,6 +353,7 @@ __device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq,
   C* Wm = T + 256;
   for (int j0 = 0; j0 < r && !failed(); j0 += 16) {
     const int bp = min(16, r - j0);
+    SubTimer spt(st, SP_QR_PANEL);
     bulk_load(P, Y + (size_t)j0 * m, (uint32_t)(sizeof(C) * bp * m));
     if (failed()) return;
     for (int jj = 0; jj < bp; ++jj) {
@@ -373,10 +406,12 @@ __device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq,
     if (j0 + bp < nq) {
       densify_panel(P, vhead, m, j0, bp);
       panel_t(P, m, j0, bp, T);
+      SubTimer sat(st, SP_QR_APPLY);
       apply_block_reflector(P, m, j0, bp, T, true, Y, j0 + bp, nq, CH, Wm);
     }
   }
   if (Q == nullptr) return;
+  SubTimer sqt(st, SP_QR_FORMQ);
   for (int e = tid(); e < m * r; e += nt()) {
     const int col = e / m, row = e - col * m;
     Q[e] = C{row == col ? R(1) : R(0), 0};

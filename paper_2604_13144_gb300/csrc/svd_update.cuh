@@ -463,6 +463,7 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
     else if (m <= 256) cross_pass_regs<8>(XA, na, XB, nbb, m, tol, thr);
     else cross_pass(XA, na, XB, nbb, m, tol, thr);
   };
+  SubTimer spt(st, SP_PASSES);
   while (sweep < a.max_sweeps) {
     if (tid() == 0) { sm.ibuf[0] = 0; sm.ibuf[6] = 0; }
     __syncthreads();
@@ -588,6 +589,7 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
   { PhaseTimer pt(st, PH_JACOBI); sweeps = jacobi(X, m, ncx, X == xs); }
   const int converged = sm.ibuf[1];
   PhaseTimer pt_trunc(st, PH_TRUNC);
+  SubTimer srt(st, SP_RANK);
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   // squared column norms (FP64 accumulation)
   const bool x_sh = X == xs;
@@ -656,6 +658,8 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
     st.alg_flops += 32.0 * dl * dc * dr + 4.0 * (14.0 * mx * mn * mn + 8.0 * mn * mn * mn);
   }
   __syncthreads();
+  srt.stop();
+  SubTimer sjt(st, SP_PROJ);
   const int k = sm.ibuf[2];
   const R renorm = (R)sm.dbuf[0];
   if (!dim_ok(k)) { fail(ST_BAD_RANK, k); return; }
@@ -672,11 +676,20 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
     __syncthreads();
     C* Bi = S(i + 1);
     const int ncol = 2 * dr;
-    for (int e = tid(); e < k * ncol; e += nt()) {
-      const int mm = e / ncol, col = e - mm * ncol;
-      C acc2 = {0, 0};
-      for (int row = 0; row < m; ++row) fma_cc(acc2, Ai[(size_t)row * k + mm], TH[(size_t)row * ncol + col]);
-      Bi[e] = scale(acc2, renorm);
+    if (a.smem_x_elems >= gemm_tile_elems(nt())) {
+      // Bi = renorm U^H theta' (the working matrix in shared memory is no longer needed)
+      const C* thp = TH;
+      block_gemm<R>(k, ncol, m, reinterpret_cast<C*>(sm.x),
+          [=](int ii, int kk) { const C u = Ai[(size_t)kk * k + ii]; return C{u.re, -u.im}; },
+          [=](int kk, int jj) { return thp[(size_t)kk * ncol + jj]; },
+          [=](int ii, int jj, C v) { Bi[(size_t)ii * ncol + jj] = scale(v, renorm); });
+    } else {
+      for (int e = tid(); e < k * ncol; e += nt()) {
+        const int mm = e / ncol, col = e - mm * ncol;
+        C acc2 = {0, 0};
+        for (int row = 0; row < m; ++row) fma_cc(acc2, Ai[(size_t)row * k + mm], TH[(size_t)row * ncol + col]);
+        Bi[e] = scale(acc2, renorm);
+      }
     }
     __syncthreads();
     if (tid() == 0) sm.dims[i + 1] = k;
@@ -695,13 +708,23 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
     __syncthreads();
     C* Ai = S(i);
     const int rows = 2 * dl;
-    for (int e = tid(); e < rows * k; e += nt()) {
-      const int row = e / k, mm = e - row * k;
-      C acc2 = {0, 0};
-      const C* th = TH + (size_t)row * ncol;
-      const C* bv = Bi + (size_t)mm * ncol;
-      for (int col = 0; col < ncol; ++col) fma_cc(acc2, bv[col], th[col]);
-      Ai[e] = scale(acc2, renorm);
+    if (a.smem_x_elems >= gemm_tile_elems(nt())) {
+      // Ai = renorm theta' V (V^H = Bi)
+      const C* thp = TH;
+      const C* bip = Bi;
+      block_gemm<R>(rows, k, ncol, reinterpret_cast<C*>(sm.x),
+          [=](int ii, int kk) { return thp[(size_t)ii * ncol + kk]; },
+          [=](int kk, int jj) { const C u = bip[(size_t)jj * ncol + kk]; return C{u.re, -u.im}; },
+          [=](int ii, int jj, C v) { Ai[(size_t)ii * k + jj] = scale(v, renorm); });
+    } else {
+      for (int e = tid(); e < rows * k; e += nt()) {
+        const int row = e / k, mm = e - row * k;
+        C acc2 = {0, 0};
+        const C* th = TH + (size_t)row * ncol;
+        const C* bv = Bi + (size_t)mm * ncol;
+        for (int col = 0; col < ncol; ++col) fma_cc(acc2, bv[col], th[col]);
+        Ai[e] = scale(acc2, renorm);
+      }
     }
     __syncthreads();
     if (tid() == 0) sm.dims[i + 1] = k;

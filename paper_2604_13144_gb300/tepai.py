@@ -59,14 +59,17 @@ class Stats(C.Structure):
                 ("max_chi", C.c_int), ("n_not_converged", C.c_int),
                 ("device_status", C.c_int * 3), ("phase_cycles", C.c_double * 8),
                 ("grid_ctas", C.c_int), ("jacobi_pairs", C.c_double),
-                ("jacobi_rotations", C.c_double)]
+                ("jacobi_rotations", C.c_double), ("subphase_cycles", C.c_double * 8)]
 
     PHASES = ("init", "sampler", "single_site", "theta", "jacobi", "truncate", "qr", "measure")
+    SUBPHASES = ("qr_panel", "qr_apply", "qr_formq", "qr_rmul", "projection", "bulk_wait",
+                 "jacobi_passes", "rank")
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
         d["device_status"] = list(self.device_status)
         d["phase_cycles"] = dict(zip(self.PHASES, list(self.phase_cycles)))
+        d["subphase_cycles"] = dict(zip(self.SUBPHASES, list(self.subphase_cycles)))
         return d
 
 
