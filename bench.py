@@ -328,7 +328,7 @@ def run_ours(a):
                   "subphase_share": {k: round(v / max(sum(phases.values()), 1.0), 4)
                                      for k, v in subphases.items()},
                   "cta_busy_frac": sum(phases.values()) / max(kms / 1e3 * SM_MAX_MHZ * 1e6 * grid, 1.0),
-                  "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi},
+                  "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi, "grid_ctas": grid},
     }
     if not a.no_tts and world == 1:
         line["tts_config1"] = tts_config1(T, W, torch, local)

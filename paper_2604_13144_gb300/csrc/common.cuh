@@ -115,7 +115,7 @@ __host__ __device__ inline size_t smem_fixed_bytes(int n, int L, int cap, int cs
   b += align_up((size_t)(n + 1) * 4, 16);          // dims
   b += align_up((size_t)L, 16);                     // flags
   b += 64 * 8;                                      // red
-  b += 16;                                          // mbarrier of the bulk copies
+  b += 32;                                          // mbarriers of the bulk copies (3 slots)
   b += align_up((size_t)2 * cap * 8, 16);           // wn
   b += align_up((size_t)2 * cap * 4, 16);           // perm
   b += align_up((size_t)n * 8, 16);                 // zval

@@ -120,6 +120,7 @@ __device__ __forceinline__ void store(void* dst, const void* src, uint32_t bytes
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 __device__ __forceinline__ void store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 }  // namespace bulk
 
 // Column handoff between the warps of one CTA: a shared-memory counter per
@@ -197,42 +198,75 @@ struct Engine {
     __syncthreads();
   }
   __device__ bool dim_ok(int d) const { return d >= 1 && d <= cap; }
-  // Bulk-copy `bytes` from global src to shared dst; every thread returns after
-  // the data has landed. The wait is bounded: on timeout the CTA records
-  // ST_COPY_TIMEOUT, waits once more (bounded) for the copy in flight, and the
-  // caller sees failed().
-  __device__ void bulk_load(void* dst, const void* src, uint32_t bytes) {
-    SubTimer sbt(st, SP_BULK);
-    const uint32_t parity = (uint32_t)(sm.ibuf[13] & 1);
-    // every thread orders its own generic writes before the async-proxy copy
+  // Bulk copies through the copy engine. A load is issued on one of three
+  // completion slots (mbarriers; the phase of slot s is bit s of ibuf[13]) and
+  // waited for later, so that it overlaps compute. Stores are issued by thread
+  // 0 as bulk async-groups: bulk_wait_store_read() frees their shared-memory
+  // sources, bulk_drain() waits until their writes are complete. A load must
+  // not read global memory written by a store that has not been drained.
+  // Every thread fences its own generic accesses before a copy is issued.
+  __device__ void bulk_issue_load(int slot, void* dst, const void* src, uint32_t bytes) {
     bulk::fence_proxy();
     __syncthreads();
-    if (tid() == 0) {
-      bulk::load(dst, src, bytes, sm.mbar);
-    }
+    if (tid() == 0) bulk::load(dst, src, bytes, sm.mbar + slot);
+  }
+  // Bounded wait for the load on `slot`: on timeout the CTA records
+  // ST_COPY_TIMEOUT, waits once more (bounded) for the copy in flight, and the
+  // caller sees failed().
+  __device__ void bulk_wait_load(int slot, uint32_t bytes) {
+    SubTimer sbt(st, SP_BULK);
+    const uint32_t parity = (uint32_t)((sm.ibuf[13] >> slot) & 1);
     bool ok = false;
-    for (int it = 0; it < (1 << 22) && !ok; ++it) ok = bulk::try_wait(sm.mbar, parity);
+    for (int it = 0; it < (1 << 22) && !ok; ++it) ok = bulk::try_wait(sm.mbar + slot, parity);
     const int timed_out = __syncthreads_or(!ok);
-    if (tid() == 0) sm.ibuf[13] += 1;
+    if (tid() == 0) sm.ibuf[13] ^= (1 << slot);
     if (timed_out) {
       bool again = false;
-      for (int it = 0; it < (1 << 22) && !again; ++it) again = bulk::try_wait(sm.mbar, parity);
+      for (int it = 0; it < (1 << 22) && !again; ++it) again = bulk::try_wait(sm.mbar + slot, parity);
       fail(ST_COPY_TIMEOUT, (int)bytes);
       return;
     }
     __syncthreads();
   }
-  // Bulk-copy `bytes` from shared src to global dst and wait for completion.
-  __device__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
-    SubTimer sbt(st, SP_BULK);
+  __device__ void bulk_issue_store(void* dst, const void* src, uint32_t bytes) {
     bulk::fence_proxy();
     __syncthreads();
+    if (tid() == 0) bulk::store(dst, src, bytes);
+  }
+  __device__ void bulk_wait_store_read() {
+    SubTimer sbt(st, SP_BULK);
+    if (tid() == 0) bulk::store_wait_read();
+    __syncthreads();
+  }
+  __device__ void bulk_drain() {
+    SubTimer sbt(st, SP_BULK);
     if (tid() == 0) {
-      bulk::store(dst, src, bytes);
       bulk::store_wait();
       bulk::fence_proxy();
     }
     __syncthreads();
+  }
+  // After a failure: bounded waits for the loads still in flight on the slots
+  // of `pend`, so that no copy lands in shared memory after the CTA has left.
+  __device__ void bulk_settle(int pend) {
+    for (int sl = 0; sl < 3; ++sl) {
+      if (!(pend & (1 << sl))) continue;
+      const uint32_t parity = (uint32_t)((sm.ibuf[13] >> sl) & 1);
+      bool ok = false;
+      for (int it = 0; it < (1 << 22) && !ok; ++it) ok = bulk::try_wait(sm.mbar + sl, parity);
+      __syncthreads();
+      if (tid() == 0) sm.ibuf[13] ^= (1 << sl);
+      __syncthreads();
+    }
+  }
+  // Synchronous forms: every thread returns after the data has landed.
+  __device__ void bulk_load(void* dst, const void* src, uint32_t bytes) {
+    bulk_issue_load(0, dst, src, bytes);
+    bulk_wait_load(0, bytes);
+  }
+  __device__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+    bulk_issue_store(dst, src, bytes);
+    bulk_drain();
   }
   // Bounded wait until column counter *ver reaches r (every lane polls). A
   // wait that runs out records ibuf[5] = 1 and returns; the pass then finishes
@@ -259,7 +293,7 @@ struct Engine {
   __device__ void householder_blocked(C* Y, int m, int nq, C* Q, double tiny2);
   __device__ void panel_t(const C* V, int m, int j0, int bp, C* T);
   __device__ void apply_block_reflector(const C* V, int m, int j0, int bp, const C* T, bool herm,
-                                        C* G, int c0, int c1, C* CH, C* Wm);
+                                        C* G, int c0, int c1, C* CH, C* CH1, C* Wm);
   // QR of Y (global or shared): blocked when Y is in global memory and the
   // staging buffer holds a panel and a chunk
   __device__ void qr_factor(C* Y, int m, int nq, C* Q, double tiny2) {

@@ -249,7 +249,7 @@ __device__ inline SmemLayout carve_smem(unsigned char* base, const KArgs& a, int
   s.dims = reinterpret_cast<int*>(base + o); o += align_up((size_t)(a.n + 1) * 4, 16);
   s.flags = base + o; o += align_up((size_t)a.L, 16);
   s.red = reinterpret_cast<double*>(base + o); o += 64 * 8;
-  s.mbar = reinterpret_cast<unsigned long long*>(base + o); o += 16;
+  s.mbar = reinterpret_cast<unsigned long long*>(base + o); o += 32;
   s.wn = reinterpret_cast<double*>(base + o); o += align_up((size_t)2 * a.chi_cap * 8, 16);
   s.perm = reinterpret_cast<int*>(base + o); o += align_up((size_t)2 * a.chi_cap * 4, 16);
   s.zval = reinterpret_cast<double*>(base + o); o += align_up((size_t)a.n * 8, 16);
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
   Engine<R> eng(a, sm, arena);
   if (threadIdx.x == 0) {
     sm.ibuf[13] = 0; sm.ibuf[14] = 0; sm.ibuf[15] = 0;
-    bulk::mbar_init(sm.mbar);
+    for (int b = 0; b < 3; ++b) bulk::mbar_init(sm.mbar + b);
   }
   __syncthreads();
   while (!eng.failed()) {

@@ -219,10 +219,12 @@ struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems, per_s
 // reports resident CTAs per SM of a (block, smem) pair. When the whole SVD
 // working matrix (2cap x 2cap) fits in shared memory it stays there; otherwise
 // it lives in global memory and column blocks are staged. Staged shapes first
-// try two samples per SM (256 threads each, staging room for one 32-column
-// Householder panel pair, which also holds two 16-column Jacobi blocks): two
-// independent CTAs fill each other's barrier and latency stalls. If two do
-// not fit, one 512-thread CTA per SM stages blocks within 128 KB.
+// try two samples per SM (256 threads each, staging room for a 16-column
+// Householder panel and one 16-column update chunk, which also holds two
+// 16-column Jacobi blocks): two independent CTAs fill each other's barrier,
+// latency and copy-wait stalls, and the modest staging leaves L1 room for
+// the global operands. If two do not fit, one 512-thread CTA per SM stages
+// blocks within 128 KB.
 template <class Occ>
 inline cudaError_t choose_launch_shape(int n, int L, int cap, int csize, int optin, Occ occ, LaunchShape& ls) {
   const size_t fixed = smem_fixed_bytes(n, L, cap, csize);
@@ -238,7 +240,7 @@ inline cudaError_t choose_launch_shape(int n, int L, int cap, int csize, int opt
   } else {
     ls.block = 256;
     ls.x_in_smem = 0;
-    ls.x_elems = 2 * cap * 36 > 2 * cap * 32 + 512 ? 2 * cap * 36 : 2 * cap * 32 + 512;
+    ls.x_elems = 2 * cap * 32 + 512;
     ls.smem = fixed + (size_t)ls.x_elems * csize;
     e = ls.smem <= (size_t)optin ? occ(ls.block, ls.smem, &per_sm) : cudaSuccess;
     if (e != cudaSuccess) return e;

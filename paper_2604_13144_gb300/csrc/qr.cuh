@@ -269,25 +269,45 @@ __device__ __noinline__ void Engine<R>::panel_t(const C* V, int m, int j0, int b
 // Apply I - V op(T) V^H to columns [c0, c1) of the global matrix G (ld m),
 // rows j0..m-1, in shared-memory chunks of 16 columns: W = V^H C,
 // W <- op(T) W (T^H when herm), C <- C - V W. V is dense in shared memory
-// (V[k*m + row], zero above its diagonal, vhead on it).
+// (V[k*m + row], zero above its diagonal, vhead on it). Chunks move by bulk
+// copies; with a second chunk buffer CH1 the load of chunk i+1 overlaps the
+// update of chunk i. Starts and ends with every earlier bulk store drained.
 template <typename R>
 __device__ void Engine<R>::apply_block_reflector(const C* V, int m, int j0, int bp, const C* T, bool herm,
-                                                 C* G, int c0, int c1, C* CH, C* Wm) {
+                                                 C* G, int c0, int c1, C* CH, C* CH1, C* Wm) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
-  for (int cs = c0; cs < c1; cs += 16) {
+  const int nch = (c1 - c0 + 15) / 16;
+  const bool dbl = CH1 != nullptr;
+  C* buf[2] = {CH, dbl ? CH1 : CH};
+  auto bytes_of = [&](int ci) { return (uint32_t)(sizeof(C) * min(16, c1 - c0 - 16 * ci) * m); };
+  bulk_drain();
+  int pend = 0;
+  if (nch > 0) {
+    bulk_issue_load(1, buf[0], G + (size_t)c0 * m, bytes_of(0));
+    pend = 2;
+  }
+  for (int ci = 0; ci < nch; ++ci) {
+    const int b = dbl ? (ci & 1) : 0;
+    const int cs = c0 + 16 * ci;
     const int cb = min(16, c1 - cs);
-    // whole columns (contiguous) by bulk copy; rows above j0 come back unchanged
-    bulk_load(CH, G + (size_t)cs * m, (uint32_t)(sizeof(C) * cb * m));
-    if (failed()) return;
+    C* ch = buf[b];
+    if (dbl && ci + 1 < nch) {
+      bulk_wait_store_read();  // the store of chunk ci-1 has read buf[b^1]
+      bulk_issue_load(1 + (b ^ 1), buf[b ^ 1], G + (size_t)(cs + 16) * m, bytes_of(ci + 1));
+      pend |= 2 << (b ^ 1);
+    }
+    bulk_wait_load(1 + b, bytes_of(ci));
+    pend &= ~(2 << b);
+    if (failed()) { bulk_settle(pend); bulk_drain(); return; }
     for (int e = w; e < bp * cb; e += nw) {
       const int k = e / cb, c = e - k * cb;
       const C* vk = V + (size_t)k * m;
-      const C* x = CH + (size_t)c * m;
+      const C* x = ch + (size_t)c * m;
       R sr = 0, si = 0;
       for (int row = j0 + k + lane; row < m; row += 32) {
-        const C a = vk[row], b = x[row];
-        sr = fma(a.re, b.re, fma(a.im, b.im, sr));
-        si = fma(a.re, b.im, fma(-a.im, b.re, si));
+        const C a = vk[row], bb = x[row];
+        sr = fma(a.re, bb.re, fma(a.im, bb.im, sr));
+        si = fma(a.re, bb.im, fma(-a.im, bb.re, si));
       }
       sr = warp_sum(sr); si = warp_sum(si);
       if (lane == 0) Wm[k * 16 + c] = C{sr, si};
@@ -310,7 +330,7 @@ __device__ void Engine<R>::apply_block_reflector(const C* V, int m, int j0, int 
     for (int e = tid(); e < cb * m; e += nt()) {
       const int c = e / m, row = e - c * m;
       if (row < j0) continue;
-      C x = CH[(size_t)c * m + row];
+      C x = ch[(size_t)c * m + row];
       const int kmax = min(bp, row - j0 + 1);
       for (int k = 0; k < kmax; ++k) {
         const C vk = V[(size_t)k * m + row];
@@ -318,10 +338,16 @@ __device__ void Engine<R>::apply_block_reflector(const C* V, int m, int j0, int 
         x.re -= vk.re * wv.re - vk.im * wv.im;
         x.im -= vk.re * wv.im + vk.im * wv.re;
       }
-      CH[(size_t)c * m + row] = x;
+      ch[(size_t)c * m + row] = x;
     }
-    bulk_store(G + (size_t)cs * m, CH, (uint32_t)(sizeof(C) * cb * m));
+    bulk_issue_store(G + (size_t)cs * m, ch, bytes_of(ci));
+    if (!dbl && ci + 1 < nch) {
+      bulk_wait_store_read();
+      bulk_issue_load(1, buf[0], G + (size_t)(cs + 16) * m, bytes_of(ci + 1));
+      pend |= 2;
+    }
   }
+  bulk_drain();
 }
 
 // Turn the factored panel in P (rows >= j0 of columns j0..j0+bp-1) into the
@@ -347,9 +373,12 @@ __device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq,
   C* vhead = reinterpret_cast<C*>(sm.hh);
   C* tau = vhead + 2 * cap;
   C* alpha = tau + 2 * cap;
+  // staging: panel P, one or two update chunks, T and W (16 x 16 each)
+  const bool dbl = (size_t)m * 48 + 512 <= (size_t)a.smem_x_elems;
   C* P = reinterpret_cast<C*>(sm.x);
   C* CH = P + (size_t)m * 16;
-  C* T = CH + (size_t)m * 16;
+  C* CH1 = dbl ? CH + (size_t)m * 16 : nullptr;
+  C* T = CH + (size_t)m * (dbl ? 32 : 16);
   C* Wm = T + 256;
   for (int j0 = 0; j0 < r && !failed(); j0 += 16) {
     const int bp = min(16, r - j0);
@@ -407,7 +436,7 @@ __device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq,
       densify_panel(P, vhead, m, j0, bp);
       panel_t(P, m, j0, bp, T);
       SubTimer sat(st, SP_QR_APPLY);
-      apply_block_reflector(P, m, j0, bp, T, true, Y, j0 + bp, nq, CH, Wm);
+      apply_block_reflector(P, m, j0, bp, T, true, Y, j0 + bp, nq, CH, CH1, Wm);
     }
   }
   if (Q == nullptr) return;
@@ -424,7 +453,7 @@ __device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq,
     if (failed()) return;
     densify_panel(P, vhead, m, j0, bp);
     panel_t(P, m, j0, bp, T);
-    apply_block_reflector(P, m, j0, bp, T, false, Q, j0, r, CH, Wm);
+    apply_block_reflector(P, m, j0, bp, T, false, Q, j0, r, CH, CH1, Wm);
   }
   (void)alpha;
 }

@@ -449,9 +449,17 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
   C* xs = reinterpret_cast<C*>(sm.x);
   // column blocks of bw: the width the staging buffer allows, at most 2 columns
   // per warp so that a block's warp-owned columns fit in registers
+  // Staged blocks: two (I, J) or, when that costs no block width, three (I and
+  // a double-buffered J whose next load overlaps the cross pass).
   int bw = 1;
+  bool prefetch = false;
   if (!x_in_smem) {
+    int bw3 = 1;
     while (4 * bw * m <= a.smem_x_elems && 2 * bw < nc) bw *= 2;
+    while (6 * bw3 * m <= a.smem_x_elems && 2 * bw3 < nc) bw3 *= 2;
+    if (bw > 2 * nw) bw = 2 * nw;
+    if (bw3 > 2 * nw) bw3 = 2 * nw;
+    prefetch = bw3 >= bw;
   } else {
     bw = nc;
   }
@@ -474,10 +482,10 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
         rr_pass(xI, m, nI, tol, thr);
         for (int J = I + 1; J < nbk; ++J) cross(xI, nI, X + (size_t)J * bw * m, min(bw, nc - J * bw));
       }
-    } else {
+    } else if (!prefetch) {
+      // blocks are contiguous column ranges of X: whole-block bulk copies
       C* sa = xs;
       C* sb = xs + (size_t)bw * m;
-      // blocks are contiguous column ranges of X: whole-block bulk copies
       for (int I = 0; I < nbk && !failed(); ++I) {
         const int nI = min(bw, nc - I * bw);
         C* gI = X + (size_t)I * bw * m;
@@ -494,6 +502,48 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
         }
         bulk_store(gI, sa, (uint32_t)(sizeof(C) * nI * m));
       }
+    } else {
+      // Blocks are contiguous column ranges of X, moved by whole-block bulk
+      // copies: block I in sa, blocks J double-buffered in sb[0] / sb[1]. The
+      // load of J+1 runs during the cross pass of J; stores complete in the
+      // background and are drained before any block is read back.
+      C* sa = xs;
+      C* sb[2] = {xs + (size_t)bw * m, xs + (size_t)2 * bw * m};
+      auto bytes_of = [&](int blk) { return (uint32_t)(sizeof(C) * min(bw, nc - blk * bw) * m); };
+      int pend = 0;  // load slots in flight
+      for (int I = 0; I < nbk && !failed(); ++I) {
+        const int nI = min(bw, nc - I * bw);
+        C* gI = X + (size_t)I * bw * m;
+        bulk_drain();
+        bulk_issue_load(0, sa, gI, bytes_of(I));
+        pend |= 1;
+        if (I + 1 < nbk) { bulk_issue_load(1, sb[0], gI + (size_t)bw * m, bytes_of(I + 1)); pend |= 2; }
+        bulk_wait_load(0, bytes_of(I));
+        pend &= ~1;
+        if (failed()) break;
+        rr_pass(sa, m, nI, tol, thr);
+        for (int J = I + 1; J < nbk; ++J) {
+          const int b = (J - I - 1) & 1;
+          const int nJ = min(bw, nc - J * bw);
+          C* gJ = X + (size_t)J * bw * m;
+          if (J + 1 < nbk) {
+            bulk_wait_store_read();  // the store of block J-1 has read sb[b^1]
+            bulk_issue_load(1 + (b ^ 1), sb[b ^ 1], gJ + (size_t)bw * m, bytes_of(J + 1));
+            pend |= 2 << (b ^ 1);
+          }
+          bulk_wait_load(1 + b, bytes_of(J));
+          pend &= ~(2 << b);
+          if (failed()) break;
+          cross(sa, nI, sb[b], nJ);
+          bulk_issue_store(gJ, sb[b], bytes_of(J));
+        }
+        if (failed()) break;
+        bulk_issue_store(gI, sa, bytes_of(I));
+      }
+      // a failed wait leaves other loads in flight: let them land before the
+      // CTA gives up its shared memory
+      if (failed()) bulk_settle(pend);
+      bulk_drain();
     }
     ++sweep;
     if (failed()) break;
