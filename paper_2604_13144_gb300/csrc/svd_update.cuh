@@ -275,6 +275,116 @@ __device__ __forceinline__ cplx<R> ld_x(const cplx<R>* p, bool in_smem) {
   }
 }
 
+// Single-precision cross pass on packed pairs: a complex element is a float2
+// and the norms, the inner product and the rotation use the paired FP32
+// instructions (two lanes of arithmetic per instruction, sm_100 family). The
+// schedule, the handoff and the rotation rule are those of cross_pass_regs;
+// FULL drops the row bounds when m = 32 RPL.
+template <int RPL, bool FULL>
+__device__ __noinline__ void cross_pass_f32(float2* XA, int na, float2* XB, int nb, int m, float tol, float thr,
+                                            int* ver, int* ibuf) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nmax = max(na, nb);
+  for (int c = threadIdx.x; c < nmax; c += blockDim.x) ver[c] = 0;
+  __syncthreads();
+  const int p0 = w, p1 = w + nw;
+  const bool o0 = p0 < nmax, o1 = p1 < nmax;
+  const bool h0 = p0 < na, h1 = p1 < na;
+  const float2 zero = make_float2(0.f, 0.f);
+  float2 a0[RPL], a1[RPL], b0[RPL], b1[RPL];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int row = lane + 32 * t;
+    const bool in = FULL || row < m;
+    a0[t] = (h0 && in) ? XA[(size_t)p0 * m + row] : zero;
+    a1[t] = (h1 && in) ? XA[(size_t)p1 * m + row] : zero;
+  }
+  auto wait = [&](const int* vp, int r) {
+    for (int it = 0; handoff::ld_acquire(vp) < r; ++it) {
+      if (it >= (1 << 22) || ibuf[5]) { ibuf[5] = 1; return; }
+    }
+  };
+  int rot = 0, chk = 0;
+  int q0 = p0, q1 = p1;
+  for (int r = 0; r < nmax && o0; ++r) {
+    wait(ver + q0, r);
+    if (o1) wait(ver + q1, r);
+    const bool d0 = h0 && q0 < nb, d1 = h1 && q1 < nb;
+    chk += (int)d0 + (int)d1;
+    float2* xb0 = XB + (size_t)q0 * m;
+    float2* xb1 = XB + (size_t)q1 * m;
+    float2 aa0 = zero, bb0 = zero, ab0 = zero, ax0 = zero, aa1 = zero, bb1 = zero, ab1 = zero, ax1 = zero;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int row = lane + 32 * t;
+      const bool in = FULL || row < m;
+      b0[t] = (d0 && in) ? xb0[row] : zero;
+      b1[t] = (d1 && in) ? xb1[row] : zero;
+      aa0 = __ffma2_rn(a0[t], a0[t], aa0);
+      bb0 = __ffma2_rn(b0[t], b0[t], bb0);
+      ab0 = __ffma2_rn(a0[t], b0[t], ab0);
+      ax0 = __ffma2_rn(a0[t], make_float2(b0[t].y, b0[t].x), ax0);
+      aa1 = __ffma2_rn(a1[t], a1[t], aa1);
+      bb1 = __ffma2_rn(b1[t], b1[t], bb1);
+      ab1 = __ffma2_rn(a1[t], b1[t], ab1);
+      ax1 = __ffma2_rn(a1[t], make_float2(b1[t].y, b1[t].x), ax1);
+    }
+    // al = |a|^2, be = |b|^2, gr + i gi = a^H b
+    float v8[8] = {aa0.x + aa0.y, bb0.x + bb0.y, ab0.x + ab0.y, ax0.x - ax0.y,
+                   aa1.x + aa1.y, bb1.x + bb1.y, ab1.x + ab1.y, ax1.x - ax1.y};
+    warp_sum8<float>(v8, lane);
+    float c0, s0, er0, ei0, c1, s1, er1, ei1;
+    const bool r0 = d0 && rot_params<float>(v8[0], v8[1], v8[2], v8[3], tol, thr, c0, s0, er0, ei0);
+    const bool r1 = d1 && rot_params<float>(v8[4], v8[5], v8[6], v8[7], tol, thr, c1, s1, er1, ei1);
+    if (r0) {
+      // w = e^{-i phi} b; a <- c a - s w; b <- s a + c w
+      const float2 e1 = make_float2(er0, er0), e2 = make_float2(-ei0, ei0);
+      const float2 cc = make_float2(c0, c0), ss = make_float2(s0, s0), ns = make_float2(-s0, -s0);
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const float2 wv = __ffma2_rn(e1, b0[t], __fmul2_rn(e2, make_float2(b0[t].y, b0[t].x)));
+        const float2 u = a0[t];
+        a0[t] = __ffma2_rn(cc, u, __fmul2_rn(ns, wv));
+        const float2 nv = __ffma2_rn(ss, u, __fmul2_rn(cc, wv));
+        const int row = lane + 32 * t;
+        if (FULL || row < m) xb0[row] = nv;
+      }
+      ++rot;
+    }
+    if (r1) {
+      const float2 e1 = make_float2(er1, er1), e2 = make_float2(-ei1, ei1);
+      const float2 cc = make_float2(c1, c1), ss = make_float2(s1, s1), ns = make_float2(-s1, -s1);
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const float2 wv = __ffma2_rn(e1, b1[t], __fmul2_rn(e2, make_float2(b1[t].y, b1[t].x)));
+        const float2 u = a1[t];
+        a1[t] = __ffma2_rn(cc, u, __fmul2_rn(ns, wv));
+        const float2 nv = __ffma2_rn(ss, u, __fmul2_rn(cc, wv));
+        const int row = lane + 32 * t;
+        if (FULL || row < m) xb1[row] = nv;
+      }
+      ++rot;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      handoff::st_release(ver + q0, r + 1);
+      if (o1) handoff::st_release(ver + q1, r + 1);
+    }
+    q0 = q0 + 1 == nmax ? 0 : q0 + 1;
+    q1 = q1 + 1 == nmax ? 0 : q1 + 1;
+  }
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int row = lane + 32 * t;
+    if (FULL || row < m) {
+      if (h0) XA[(size_t)p0 * m + row] = a0[t];
+      if (h1) XA[(size_t)p1 * m + row] = a1[t];
+    }
+  }
+  if (lane == 0) { if (rot) atomicAdd(&ibuf[0], rot); if (chk) atomicAdd(&ibuf[6], chk); }
+  __syncthreads();
+}
+
 // Cross pairs of blocks A and B (na, nb <= 2 * warps) with the warp-owned A
 // columns held in registers: warp w owns A slots w and w + nw for the whole
 // pass; in round r slot p meets B column (p + r) mod nmax. Only B columns move
@@ -285,6 +395,13 @@ __device__ __forceinline__ cplx<R> ld_x(const cplx<R>* p, bool in_smem) {
 template <typename R>
 template <int RPL>
 __device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
+  if constexpr (sizeof(R) == 4) {
+    float2* xa = reinterpret_cast<float2*>(XA);
+    float2* xb = reinterpret_cast<float2*>(XB);
+    if (m == 32 * RPL) cross_pass_f32<RPL, true>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf);
+    else cross_pass_f32<RPL, false>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf);
+    return;
+  }
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int nmax = max(na, nb);
   int* ver = sm.perm;
