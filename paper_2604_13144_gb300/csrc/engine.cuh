@@ -22,6 +22,64 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Warp sums of several scalars at once by a transposing butterfly: each xor
+// level halves the number of values a lane carries (it keeps one half and
+// sends the other to its partner), so 4 values take 2 + 1 shuffles and 8 take
+// 4 + 2 + 1 before the last levels reduce the single survivor. Every lane ends
+// with the totals, read from one lane each, so all lanes hold bit-identical
+// sums and take the same branch on them.
+template <typename R>
+__device__ __forceinline__ void warp_sum4(R v[4], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8;
+  R w[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const R send = b4 ? v[j] : v[j + 2], keep = b4 ? v[j + 2] : v[j];
+    w[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  // w[j] carries value j + 2*b4
+  R z;
+  {
+    const R send = b3 ? w[0] : w[1], keep = b3 ? w[1] : w[0];
+    z = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  // z carries value b3 + 2*b4, summed over lanes that differ in bits 4 and 3
+  z += __shfl_xor_sync(0xffffffffu, z, 4);
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = __shfl_sync(0xffffffffu, z, 8 * j);
+}
+
+template <typename R>
+__device__ __forceinline__ void warp_sum8(R v[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  R w[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const R send = b4 ? v[j] : v[j + 4], keep = b4 ? v[j + 4] : v[j];
+    w[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  // w[j] carries value j + 4*b4
+  R u[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const R send = b3 ? w[j] : w[j + 2], keep = b3 ? w[j + 2] : w[j];
+    u[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  // u[j] carries value j + 2*b3 + 4*b4
+  R z;
+  {
+    const R send = b2 ? u[0] : u[1], keep = b2 ? u[1] : u[0];
+    z = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  // z carries value b2 + 2*b3 + 4*b4, summed over lanes that differ in bits 4..2
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __shfl_sync(0xffffffffu, z, 4 * j);
+}
+
 // Sum over the CTA; every thread gets the result. `red` holds >= 33 doubles.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);

@@ -266,6 +266,113 @@ __device__ __noinline__ void Engine<R>::panel_t(const C* V, int m, int j0, int b
   __syncthreads();
 }
 
+// Single-precision compute of one block-reflector chunk (cb <= 16 columns of
+// C in shared memory, m = 32 RPL rows at most): W = V^H C, W <- op(T) W,
+// C <- C - V W. For W, warp w keeps the rows of reflectors k = w and w + nw in
+// registers across the chunk's columns and forms both inner products with
+// paired FP32 FMA; the update gives each thread a 4 x 4 block of (rows,
+// columns) so that every loaded V or W element feeds four products.
+template <int RPL>
+__device__ __noinline__ void apply_chunk_f32(const float2* V, int m, int bp, const float2* T, bool herm,
+                                             float2* ch, int cb, float2* Wm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int k0 = w; k0 < bp; k0 += 2 * nw) {
+    const int k1 = k0 + nw;
+    const bool has1 = k1 < bp;
+    float2 v0[RPL], v1[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int row = lane + 32 * t;
+      v0[t] = row < m ? V[(size_t)k0 * m + row] : zero;
+      v1[t] = (has1 && row < m) ? V[(size_t)k1 * m + row] : zero;
+    }
+    for (int c = 0; c < cb; ++c) {
+      const float2* x = ch + (size_t)c * m;
+      float2 r0 = zero, i0 = zero, r1 = zero, i1 = zero;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int row = lane + 32 * t;
+        const float2 xv = row < m ? x[row] : zero;
+        const float2 xs = make_float2(xv.y, xv.x);
+        // conj(v) x = (v.re x.re + v.im x.im) + i (v.re x.im - v.im x.re)
+        r0 = __ffma2_rn(v0[t], xv, r0);
+        i0 = __ffma2_rn(v0[t], xs, i0);
+        r1 = __ffma2_rn(v1[t], xv, r1);
+        i1 = __ffma2_rn(v1[t], xs, i1);
+      }
+      float s4[4] = {r0.x + r0.y, i0.x - i0.y, r1.x + r1.y, i1.x - i1.y};
+      warp_sum4<float>(s4, lane);
+      if (lane == 0) {
+        Wm[k0 * 16 + c] = make_float2(s4[0], s4[1]);
+        if (has1) Wm[k1 * 16 + c] = make_float2(s4[2], s4[3]);
+      }
+    }
+  }
+  __syncthreads();
+  // W2 = op(T) W, kept in registers of threads (k, c), then written back
+  float2 w2 = zero;
+  const int kk = threadIdx.x / 16, cc = threadIdx.x % 16;
+  const bool act = threadIdx.x < 256 && kk < bp && cc < cb;
+  if (act) {
+    cplx<float> acc = {0.f, 0.f};
+    const cplx<float>* Tc = reinterpret_cast<const cplx<float>*>(T);
+    const cplx<float>* Wc = reinterpret_cast<const cplx<float>*>(Wm);
+    if (herm) {
+      for (int q = 0; q <= kk; ++q) fma_cc(acc, Tc[q * 16 + kk], Wc[q * 16 + cc]);
+    } else {
+      for (int q = kk; q < bp; ++q) fma_c(acc, Tc[kk * 16 + q], Wc[q * 16 + cc]);
+    }
+    w2 = make_float2(acc.re, acc.im);
+  }
+  __syncthreads();
+  if (act) Wm[kk * 16 + cc] = w2;
+  __syncthreads();
+  // C <- C - V W: item (rbase, column group) covers rows rbase + R4 i (i < 4)
+  // and columns 4 g .. 4 g + 3
+  const int R4 = (m + 3) / 4, ng = (cb + 3) / 4;
+  for (int e = threadIdx.x; e < R4 * ng; e += blockDim.x) {
+    const int g = e / R4, rbase = e - g * R4;
+    float accr[4][4], acci[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { accr[i][j] = 0.f; acci[i][j] = 0.f; }
+    for (int k = 0; k < bp; ++k) {
+      float2 vv[4], ww[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = rbase + R4 * i;
+        vv[i] = row < m ? V[(size_t)k * m + row] : zero;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) ww[j] = Wm[k * 16 + 4 * g + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          accr[i][j] = fmaf(vv[i].x, ww[j].x, fmaf(-vv[i].y, ww[j].y, accr[i][j]));
+          acci[i][j] = fmaf(vv[i].x, ww[j].y, fmaf(vv[i].y, ww[j].x, acci[i][j]));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int row = rbase + R4 * i;
+      if (row >= m) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = 4 * g + j;
+        if (c < cb) {
+          float2 x = ch[(size_t)c * m + row];
+          x.x -= accr[i][j];
+          x.y -= acci[i][j];
+          ch[(size_t)c * m + row] = x;
+        }
+      }
+    }
+  }
+}
+
 // Apply I - V op(T) V^H to columns [c0, c1) of the global matrix G (ld m),
 // rows j0..m-1, in shared-memory chunks of 16 columns: W = V^H C,
 // W <- op(T) W (T^H when herm), C <- C - V W. V is dense in shared memory
@@ -299,6 +406,19 @@ __device__ void Engine<R>::apply_block_reflector(const C* V, int m, int j0, int 
     bulk_wait_load(1 + b, bytes_of(ci));
     pend &= ~(2 << b);
     if (failed()) { bulk_settle(pend); bulk_drain(); return; }
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+      const float2* Vf = reinterpret_cast<const float2*>(V);
+      const float2* Tf = reinterpret_cast<const float2*>(T);
+      float2* chf = reinterpret_cast<float2*>(ch);
+      float2* Wf = reinterpret_cast<float2*>(Wm);
+      done = true;
+      if (m <= 64) apply_chunk_f32<2>(Vf, m, bp, Tf, herm, chf, cb, Wf);
+      else if (m <= 128) apply_chunk_f32<4>(Vf, m, bp, Tf, herm, chf, cb, Wf);
+      else if (m <= 256) apply_chunk_f32<8>(Vf, m, bp, Tf, herm, chf, cb, Wf);
+      else done = false;
+    }
+    if (!done) {
     for (int e = w; e < bp * cb; e += nw) {
       const int k = e / cb, c = e - k * cb;
       const C* vk = V + (size_t)k * m;
@@ -339,6 +459,7 @@ __device__ void Engine<R>::apply_block_reflector(const C* V, int m, int j0, int 
         x.im -= vk.re * wv.im + vk.im * wv.re;
       }
       ch[(size_t)c * m + row] = x;
+    }
     }
     bulk_issue_store(G + (size_t)cs * m, ch, bytes_of(ci));
     if (!dbl && ci + 1 < nch) {
