@@ -142,6 +142,9 @@ __device__ __noinline__ void Engine<R>::measure_z(double* zout) {
   C* E = TH;
   C* Tm = TH + (size_t)cap * cap;
   double nrm = 1.0;
+  // dense products through shared-memory tiles when the staging room holds one
+  const bool use_gemm = a.smem_x_elems >= gemm_tile_elems(nt());
+  C* tile = reinterpret_cast<C*>(sm.x);
   // rightward sweep
   {
     const int d = sm.dims[c];
@@ -150,11 +153,22 @@ __device__ __noinline__ void Engine<R>::measure_z(double* zout) {
     for (int i = c; i < n; ++i) {
       const int dl = sm.dims[i], dr = sm.dims[i + 1];
       const C* A = S(i);
-      for (int e = tid(); e < 2 * dl * dr; e += nt()) {
-        const int s = e / (dl * dr), rem = e - s * dl * dr, aa = rem / dr, bb = rem - aa * dr;
-        C acc = {0, 0};
-        for (int q = 0; q < dl; ++q) fma_c(acc, E[(size_t)aa * dl + q], A[(size_t)(q * 2 + s) * dr + bb]);
-        Tm[e] = acc;
+      if (use_gemm) {
+        // Tm^s[aa][bb] = sum_q E[aa][q] A[q][s][bb]: columns j = s dr + bb of A's rows
+        block_gemm<R>(dl, 2 * dr, dl, tile,
+            [=](int ii, int kk) { return E[(size_t)ii * dl + kk]; },
+            [=](int kk, int jj) { return A[(size_t)kk * 2 * dr + jj]; },
+            [=](int ii, int jj, C v) {
+              const int s = jj >= dr, bb = jj - s * dr;
+              Tm[(size_t)s * dl * dr + (size_t)ii * dr + bb] = v;
+            });
+      } else {
+        for (int e = tid(); e < 2 * dl * dr; e += nt()) {
+          const int s = e / (dl * dr), rem = e - s * dl * dr, aa = rem / dr, bb = rem - aa * dr;
+          C acc = {0, 0};
+          for (int q = 0; q < dl; ++q) fma_c(acc, E[(size_t)aa * dl + q], A[(size_t)(q * 2 + s) * dr + bb]);
+          Tm[e] = acc;
+        }
       }
       __syncthreads();
       double zp = 0.0, np_ = 0.0;
@@ -170,17 +184,30 @@ __device__ __noinline__ void Engine<R>::measure_z(double* zout) {
       if (i == c) nrm = nn;
       if (tid() == 0) sm.zval[i] = z;
       if (i + 1 < n) {
-        for (int e = tid(); e < dr * dr; e += nt()) {
-          const int b1 = e / dr, b2 = e - b1 * dr;
-          C acc = {0, 0};
-          for (int s = 0; s < 2; ++s)
-            for (int q = 0; q < dl; ++q)
-              fma_cc(acc, A[(size_t)(q * 2 + s) * dr + b1], Tm[(size_t)s * dl * dr + (size_t)q * dr + b2]);
-          XG[e] = acc;
+        if (use_gemm) {
+          // E'[b1][b2] = sum_{s,q} conj(A[q][s][b1]) Tm^s[q][b2], k = s dl + q (E is not read here)
+          block_gemm<R>(dr, dr, 2 * dl, tile,
+              [=](int ii, int kk) {
+                const int s = kk >= dl, q = kk - s * dl;
+                const C u = A[(size_t)(q * 2 + s) * dr + ii];
+                return C{u.re, -u.im};
+              },
+              [=](int kk, int jj) { return Tm[(size_t)kk * dr + jj]; },
+              [=](int ii, int jj, C v) { E[(size_t)ii * dr + jj] = v; });
+          __syncthreads();
+        } else {
+          for (int e = tid(); e < dr * dr; e += nt()) {
+            const int b1 = e / dr, b2 = e - b1 * dr;
+            C acc = {0, 0};
+            for (int s = 0; s < 2; ++s)
+              for (int q = 0; q < dl; ++q)
+                fma_cc(acc, A[(size_t)(q * 2 + s) * dr + b1], Tm[(size_t)s * dl * dr + (size_t)q * dr + b2]);
+            XG[e] = acc;
+          }
+          __syncthreads();
+          for (int e = tid(); e < dr * dr; e += nt()) E[e] = XG[e];
+          __syncthreads();
         }
-        __syncthreads();
-        for (int e = tid(); e < dr * dr; e += nt()) E[e] = XG[e];
-        __syncthreads();
       }
     }
   }
@@ -193,12 +220,20 @@ __device__ __noinline__ void Engine<R>::measure_z(double* zout) {
       const int dl = sm.dims[i], dr = sm.dims[i + 1];
       const C* A = S(i);
       // U^s[a][b'] = sum_b A[a][s][b] F[b][b']
-      for (int e = tid(); e < 2 * dl * dr; e += nt()) {
-        const int s = e / (dl * dr), rem = e - s * dl * dr, aa = rem / dr, bb = rem - aa * dr;
-        C acc = {0, 0};
-        const C* ar = A + (size_t)(aa * 2 + s) * dr;
-        for (int q = 0; q < dr; ++q) fma_c(acc, ar[q], E[(size_t)q * dr + bb]);
-        Tm[e] = acc;
+      if (use_gemm) {
+        // rows i = 2 a + s of A times F
+        block_gemm<R>(2 * dl, dr, dr, tile,
+            [=](int ii, int kk) { return A[(size_t)ii * dr + kk]; },
+            [=](int kk, int jj) { return E[(size_t)kk * dr + jj]; },
+            [=](int ii, int jj, C v) { Tm[(size_t)(ii & 1) * dl * dr + (size_t)(ii >> 1) * dr + jj] = v; });
+      } else {
+        for (int e = tid(); e < 2 * dl * dr; e += nt()) {
+          const int s = e / (dl * dr), rem = e - s * dl * dr, aa = rem / dr, bb = rem - aa * dr;
+          C acc = {0, 0};
+          const C* ar = A + (size_t)(aa * 2 + s) * dr;
+          for (int q = 0; q < dr; ++q) fma_c(acc, ar[q], E[(size_t)q * dr + bb]);
+          Tm[e] = acc;
+        }
       }
       __syncthreads();
       if (i < c) {
@@ -214,17 +249,33 @@ __device__ __noinline__ void Engine<R>::measure_z(double* zout) {
       }
       if (i == 0) break;
       // F'[a][a'] = sum_s sum_b' U^s[a][b'] conj(A[a'][s][b'])
-      for (int e = tid(); e < dl * dl; e += nt()) {
-        const int a1 = e / dl, a2 = e - a1 * dl;
-        C acc = {0, 0};
-        for (int s = 0; s < 2; ++s)
-          for (int q = 0; q < dr; ++q)
-            fma_cc(acc, A[(size_t)(a2 * 2 + s) * dr + q], Tm[(size_t)s * dl * dr + (size_t)a1 * dr + q]);
-        XG[e] = acc;
+      if (use_gemm) {
+        // k = s dr + q (F is not read here)
+        block_gemm<R>(dl, dl, 2 * dr, tile,
+            [=](int ii, int kk) {
+              const int s = kk >= dr, q = kk - s * dr;
+              return Tm[(size_t)s * dl * dr + (size_t)ii * dr + q];
+            },
+            [=](int kk, int jj) {
+              const int s = kk >= dr, q = kk - s * dr;
+              const C u = A[(size_t)(jj * 2 + s) * dr + q];
+              return C{u.re, -u.im};
+            },
+            [=](int ii, int jj, C v) { E[(size_t)ii * dl + jj] = v; });
+        __syncthreads();
+      } else {
+        for (int e = tid(); e < dl * dl; e += nt()) {
+          const int a1 = e / dl, a2 = e - a1 * dl;
+          C acc = {0, 0};
+          for (int s = 0; s < 2; ++s)
+            for (int q = 0; q < dr; ++q)
+              fma_cc(acc, A[(size_t)(a2 * 2 + s) * dr + q], Tm[(size_t)s * dl * dr + (size_t)a1 * dr + q]);
+          XG[e] = acc;
+        }
+        __syncthreads();
+        for (int e = tid(); e < dl * dl; e += nt()) E[e] = XG[e];
+        __syncthreads();
       }
-      __syncthreads();
-      for (int e = tid(); e < dl * dl; e += nt()) E[e] = XG[e];
-      __syncthreads();
     }
   }
   __syncthreads();

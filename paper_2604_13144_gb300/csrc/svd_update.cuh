@@ -18,15 +18,34 @@ __device__ __noinline__ void Engine<R>::form_theta(int i, const C g[16], bool en
   const C* A = S(i);
   const C* B = S(i + 1);
   const int m = 2 * dl, ncol = 2 * dr;
+  // The shared-memory staging room is free before the SVD: when it holds a
+  // GEMM tile, T[(a,s),(t,b)] = sum_c A_i[a,s,c] A_{i+1}[c,t,b] goes into TH
+  // first (rows 2a+s, columns t dr + b: the natural layouts of both sites) and
+  // the gate pass below reads it back in place.
+  const bool use_gemm = a.smem_x_elems >= gemm_tile_elems(nt()) && X != TH;
+  if (use_gemm) {
+    C* thp = TH;
+    block_gemm<R>(m, ncol, dc, reinterpret_cast<C*>(sm.x),
+        [=](int ii, int kk) { return A[(size_t)ii * dc + kk]; },
+        [=](int kk, int jj) { return B[(size_t)kk * ncol + jj]; },
+        [=](int ii, int jj, C v) { thp[(size_t)ii * ncol + jj] = v; });
+    __syncthreads();
+  }
   for (int e = tid(); e < dl * dr; e += nt()) {
     const int aa = e / dr, bb = e - aa * dr;
     C t[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    const C* a0p = A + (size_t)(aa * 2) * dc;
-    const C* a1p = a0p + dc;
-    for (int c = 0; c < dc; ++c) {
-      const C a0 = a0p[c], a1 = a1p[c];
-      const C b0 = B[(size_t)(c * 2) * dr + bb], b1 = B[(size_t)(c * 2 + 1) * dr + bb];
-      fma_c(t[0], a0, b0); fma_c(t[1], a0, b1); fma_c(t[2], a1, b0); fma_c(t[3], a1, b1);
+    if (use_gemm) {
+      // T[(a,s'),(t',b)] at row 2a+s', column t' dr + b; index s4 = 2 s' + t'
+#pragma unroll
+      for (int s4 = 0; s4 < 4; ++s4) t[s4] = TH[(size_t)(aa * 2 + (s4 >> 1)) * ncol + (s4 & 1) * dr + bb];
+    } else {
+      const C* a0p = A + (size_t)(aa * 2) * dc;
+      const C* a1p = a0p + dc;
+      for (int c = 0; c < dc; ++c) {
+        const C a0 = a0p[c], a1 = a1p[c];
+        const C b0 = B[(size_t)(c * 2) * dr + bb], b1 = B[(size_t)(c * 2 + 1) * dr + bb];
+        fma_c(t[0], a0, b0); fma_c(t[1], a0, b1); fma_c(t[2], a1, b0); fma_c(t[3], a1, b1);
+      }
     }
 #pragma unroll
     for (int s4 = 0; s4 < 4; ++s4) {
@@ -219,21 +238,36 @@ __device__ __forceinline__ cplx<R> ld_x(const cplx<R>* p, bool in_smem) {
 
 // Single-precision cross pass on packed pairs: a complex element is a float2
 // and the norms, the inner product and the rotation use the paired FP32
-// instructions (two lanes of arithmetic per instruction, sm_100 family). The
-// schedule, the handoff and the rotation rule are those of cross_pass_regs;
-// FULL drops the row bounds when m = 32 RPL.
+// instructions (two lanes of arithmetic per instruction, sm_100 family).
+// FULL drops the row bounds when m = 32 RPL. B elements are not kept in
+// registers between the inner products and the rotation (they are read again
+// from shared memory), which leaves the A columns the only long-lived arrays.
+//
+// Schedule: the warps form G independent groups (G divides nmax and the warp
+// count); group g owns A slots g H .. g H + H - 1 (H = nmax / G), two per warp.
+// In phase ph the group meets the B columns of part (g + ph) mod G: in local
+// round r its slot pl meets B column part H + (pl + r) mod H. Every B column is
+// touched by exactly one slot in each global round R = ph H + r, and a slot
+// waits only until its columns have completed round R - 1 (ver[q], acquire /
+// release). G = 1 is one cyclic ring of warps; G > 1 gives G rings that run
+// independently (measured no faster at chi = 128 with two CTAs per SM, so the
+// default is 1).
 template <int RPL, bool FULL>
 __device__ __noinline__ void cross_pass_f32(float2* XA, int na, float2* XB, int nb, int m, float tol, float thr,
-                                            int* ver, int* ibuf) {
+                                            int* ver, int* ibuf, int groups) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nmax = max(na, nb);
+  const int G = (groups > 1 && nmax % groups == 0 && nw % groups == 0) ? groups : 1;
+  const int H = nmax / G, WG = nw / G;
+  const int g = w / WG, wl = w - g * WG;
   for (int c = threadIdx.x; c < nmax; c += blockDim.x) ver[c] = 0;
   __syncthreads();
-  const int p0 = w, p1 = w + nw;
-  const bool o0 = p0 < nmax, o1 = p1 < nmax;
-  const bool h0 = p0 < na, h1 = p1 < na;
+  const int pl0 = wl, pl1 = wl + WG;
+  const bool o0 = pl0 < H, o1 = pl1 < H;  // slots this warp owns
+  const int p0 = g * H + pl0, p1 = g * H + pl1;
+  const bool h0 = o0 && p0 < na, h1 = o1 && p1 < na;
   const float2 zero = make_float2(0.f, 0.f);
-  float2 a0[RPL], a1[RPL], b0[RPL], b1[RPL];
+  float2 a0[RPL], a1[RPL];
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     const int row = lane + 32 * t;
@@ -247,73 +281,80 @@ __device__ __noinline__ void cross_pass_f32(float2* XA, int na, float2* XB, int 
     }
   };
   int rot = 0, chk = 0;
-  int q0 = p0, q1 = p1;
-  for (int r = 0; r < nmax && o0; ++r) {
-    wait(ver + q0, r);
-    if (o1) wait(ver + q1, r);
-    const bool d0 = h0 && q0 < nb, d1 = h1 && q1 < nb;
-    chk += (int)d0 + (int)d1;
-    float2* xb0 = XB + (size_t)q0 * m;
-    float2* xb1 = XB + (size_t)q1 * m;
-    float2 aa0 = zero, bb0 = zero, ab0 = zero, ax0 = zero, aa1 = zero, bb1 = zero, ab1 = zero, ax1 = zero;
-#pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-      const int row = lane + 32 * t;
-      const bool in = FULL || row < m;
-      b0[t] = (d0 && in) ? xb0[row] : zero;
-      b1[t] = (d1 && in) ? xb1[row] : zero;
-      aa0 = __ffma2_rn(a0[t], a0[t], aa0);
-      bb0 = __ffma2_rn(b0[t], b0[t], bb0);
-      ab0 = __ffma2_rn(a0[t], b0[t], ab0);
-      ax0 = __ffma2_rn(a0[t], make_float2(b0[t].y, b0[t].x), ax0);
-      aa1 = __ffma2_rn(a1[t], a1[t], aa1);
-      bb1 = __ffma2_rn(b1[t], b1[t], bb1);
-      ab1 = __ffma2_rn(a1[t], b1[t], ab1);
-      ax1 = __ffma2_rn(a1[t], make_float2(b1[t].y, b1[t].x), ax1);
-    }
-    // al = |a|^2, be = |b|^2, gr + i gi = a^H b
-    float v8[8] = {aa0.x + aa0.y, bb0.x + bb0.y, ab0.x + ab0.y, ax0.x - ax0.y,
-                   aa1.x + aa1.y, bb1.x + bb1.y, ab1.x + ab1.y, ax1.x - ax1.y};
-    warp_sum8<float>(v8, lane);
-    float c0, s0, er0, ei0, c1, s1, er1, ei1;
-    const bool r0 = d0 && rot_params<float>(v8[0], v8[1], v8[2], v8[3], tol, thr, c0, s0, er0, ei0);
-    const bool r1 = d1 && rot_params<float>(v8[4], v8[5], v8[6], v8[7], tol, thr, c1, s1, er1, ei1);
-    if (r0) {
-      // w = e^{-i phi} b; a <- c a - s w; b <- s a + c w
-      const float2 e1 = make_float2(er0, er0), e2 = make_float2(-ei0, ei0);
-      const float2 cc = make_float2(c0, c0), ss = make_float2(s0, s0), ns = make_float2(-s0, -s0);
+  for (int ph = 0; ph < G && o0; ++ph) {
+    const int part = (g + ph) % G;
+    int lq0 = pl0, lq1 = pl1 < H ? pl1 : 0;
+    for (int r = 0; r < H; ++r) {
+      const int R = ph * H + r;
+      const int q0 = part * H + lq0, q1 = part * H + lq1;
+      wait(ver + q0, R);
+      if (o1) wait(ver + q1, R);
+      const bool d0 = h0 && q0 < nb, d1 = h1 && q1 < nb;
+      chk += (int)d0 + (int)d1;
+      float2* xb0 = XB + (size_t)q0 * m;
+      float2* xb1 = XB + (size_t)q1 * m;
+      float2 aa0 = zero, bb0 = zero, ab0 = zero, ax0 = zero, aa1 = zero, bb1 = zero, ab1 = zero, ax1 = zero;
 #pragma unroll
       for (int t = 0; t < RPL; ++t) {
-        const float2 wv = __ffma2_rn(e1, b0[t], __fmul2_rn(e2, make_float2(b0[t].y, b0[t].x)));
-        const float2 u = a0[t];
-        a0[t] = __ffma2_rn(cc, u, __fmul2_rn(ns, wv));
-        const float2 nv = __ffma2_rn(ss, u, __fmul2_rn(cc, wv));
         const int row = lane + 32 * t;
-        if (FULL || row < m) xb0[row] = nv;
+        const bool in = FULL || row < m;
+        const float2 b0 = (d0 && in) ? xb0[row] : zero;
+        const float2 b1 = (d1 && in) ? xb1[row] : zero;
+        aa0 = __ffma2_rn(a0[t], a0[t], aa0);
+        bb0 = __ffma2_rn(b0, b0, bb0);
+        ab0 = __ffma2_rn(a0[t], b0, ab0);
+        ax0 = __ffma2_rn(a0[t], make_float2(b0.y, b0.x), ax0);
+        aa1 = __ffma2_rn(a1[t], a1[t], aa1);
+        bb1 = __ffma2_rn(b1, b1, bb1);
+        ab1 = __ffma2_rn(a1[t], b1, ab1);
+        ax1 = __ffma2_rn(a1[t], make_float2(b1.y, b1.x), ax1);
       }
-      ++rot;
-    }
-    if (r1) {
-      const float2 e1 = make_float2(er1, er1), e2 = make_float2(-ei1, ei1);
-      const float2 cc = make_float2(c1, c1), ss = make_float2(s1, s1), ns = make_float2(-s1, -s1);
+      // al = |a|^2, be = |b|^2, gr + i gi = a^H b
+      float v8[8] = {aa0.x + aa0.y, bb0.x + bb0.y, ab0.x + ab0.y, ax0.x - ax0.y,
+                     aa1.x + aa1.y, bb1.x + bb1.y, ab1.x + ab1.y, ax1.x - ax1.y};
+      warp_sum8<float>(v8, lane);
+      float c0, s0, er0, ei0, c1, s1, er1, ei1;
+      const bool r0 = d0 && rot_params<float>(v8[0], v8[1], v8[2], v8[3], tol, thr, c0, s0, er0, ei0);
+      const bool r1 = d1 && rot_params<float>(v8[4], v8[5], v8[6], v8[7], tol, thr, c1, s1, er1, ei1);
+      if (r0) {
+        // w = e^{-i phi} b; a <- c a - s w; b <- s a + c w
+        const float2 e1 = make_float2(er0, er0), e2 = make_float2(-ei0, ei0);
+        const float2 cc = make_float2(c0, c0), ss = make_float2(s0, s0), ns = make_float2(-s0, -s0);
 #pragma unroll
-      for (int t = 0; t < RPL; ++t) {
-        const float2 wv = __ffma2_rn(e1, b1[t], __fmul2_rn(e2, make_float2(b1[t].y, b1[t].x)));
-        const float2 u = a1[t];
-        a1[t] = __ffma2_rn(cc, u, __fmul2_rn(ns, wv));
-        const float2 nv = __ffma2_rn(ss, u, __fmul2_rn(cc, wv));
-        const int row = lane + 32 * t;
-        if (FULL || row < m) xb1[row] = nv;
+        for (int t = 0; t < RPL; ++t) {
+          const int row = lane + 32 * t;
+          if (!(FULL || row < m)) continue;
+          const float2 b = xb0[row];
+          const float2 wv = __ffma2_rn(e1, b, __fmul2_rn(e2, make_float2(b.y, b.x)));
+          const float2 u = a0[t];
+          a0[t] = __ffma2_rn(cc, u, __fmul2_rn(ns, wv));
+          xb0[row] = __ffma2_rn(ss, u, __fmul2_rn(cc, wv));
+        }
+        ++rot;
       }
-      ++rot;
+      if (r1) {
+        const float2 e1 = make_float2(er1, er1), e2 = make_float2(-ei1, ei1);
+        const float2 cc = make_float2(c1, c1), ss = make_float2(s1, s1), ns = make_float2(-s1, -s1);
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          const int row = lane + 32 * t;
+          if (!(FULL || row < m)) continue;
+          const float2 b = xb1[row];
+          const float2 wv = __ffma2_rn(e1, b, __fmul2_rn(e2, make_float2(b.y, b.x)));
+          const float2 u = a1[t];
+          a1[t] = __ffma2_rn(cc, u, __fmul2_rn(ns, wv));
+          xb1[row] = __ffma2_rn(ss, u, __fmul2_rn(cc, wv));
+        }
+        ++rot;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        handoff::st_release(ver + q0, R + 1);
+        if (o1) handoff::st_release(ver + q1, R + 1);
+      }
+      lq0 = lq0 + 1 == H ? 0 : lq0 + 1;
+      lq1 = lq1 + 1 == H ? 0 : lq1 + 1;
     }
-    __syncwarp();
-    if (lane == 0) {
-      handoff::st_release(ver + q0, r + 1);
-      if (o1) handoff::st_release(ver + q1, r + 1);
-    }
-    q0 = q0 + 1 == nmax ? 0 : q0 + 1;
-    q1 = q1 + 1 == nmax ? 0 : q1 + 1;
   }
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
@@ -340,8 +381,8 @@ __device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, in
   if constexpr (sizeof(R) == 4) {
     float2* xa = reinterpret_cast<float2*>(XA);
     float2* xb = reinterpret_cast<float2*>(XB);
-    if (m == 32 * RPL) cross_pass_f32<RPL, true>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf);
-    else cross_pass_f32<RPL, false>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf);
+    if (m == 32 * RPL) cross_pass_f32<RPL, true>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf, a.jac_groups);
+    else cross_pass_f32<RPL, false>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf, a.jac_groups);
     return;
   }
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
