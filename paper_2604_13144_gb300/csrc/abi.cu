@@ -45,12 +45,6 @@ NumCfg num_cfg(int precision) {
 
 // QR preconditioning of the Jacobi SVD: on unless TEPAI_JACOBI_PRECONDITION=0
 // (kept switchable for A/B timing of the two SVD variants).
-int jacobi_groups() {
-  const char* e = std::getenv("TEPAI_JACOBI_GROUPS");
-  if (e && (e[0] == '1' || e[0] == '2' || e[0] == '4') && e[1] == 0) return e[0] - '0';
-  return 1;
-}
-
 int jacobi_precondition() {
   const char* e = std::getenv("TEPAI_JACOBI_PRECONDITION");
   return (e && e[0] == '0') ? 0 : 1;
@@ -175,7 +169,6 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   a.status = reinterpret_cast<int*>(base + L.status);
   a.x_in_smem = ls.x_in_smem; a.smem_x_elems = ls.x_elems;
   a.precondition = jacobi_precondition();
-  a.jac_groups = jacobi_groups();
   pr.precision = Q->precision; pr.grid = ls.grid; pr.block = ls.block; pr.smem = ls.smem;
   pr.n_samples = Q->n_samples; pr.M = hp.M; pr.n_obs = hp.n_obs;
   pr.gnorm = reinterpret_cast<double*>(base + L.gnorm);

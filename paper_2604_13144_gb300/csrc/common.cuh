@@ -101,7 +101,6 @@ struct KArgs {
   int smem_x_elems;          // capacity of that buffer (complex elements)
   int* status;               // [4]: first failure (code, detail, sample, 0); 0 = ok
   int precondition;          // 1 = QR-preconditioned Jacobi where the shapes allow it
-  int jac_groups;            // independent warp groups of a Jacobi cross pass (1, 2 or 4)
 };
 
 // Device status codes. A CTA that detects a broken invariant records the first

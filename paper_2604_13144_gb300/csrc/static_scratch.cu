@@ -126,7 +126,6 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
   a.status = reinterpret_cast<int*>(base + o_status);
   a.x_in_smem = x_in_smem; a.smem_x_elems = x_elems;
   a.precondition = 1;
-  a.jac_groups = 1;
   const cudaError_t le = Q->precision == TEPAI_FP64 ? launch_ensemble_f64(a, (int)grid, block, smem, st)
                                                     : launch_ensemble_f32(a, (int)grid, block, smem, st);
   if (le != cudaSuccess) return TEPAI_ERR_CUDA;

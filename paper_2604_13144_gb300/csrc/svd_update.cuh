@@ -236,38 +236,32 @@ __device__ __forceinline__ cplx<R> ld_x(const cplx<R>* p, bool in_smem) {
   }
 }
 
-// Single-precision cross pass on packed pairs: a complex element is a float2
-// and the norms, the inner product and the rotation use the paired FP32
-// instructions (two lanes of arithmetic per instruction, sm_100 family).
-// FULL drops the row bounds when m = 32 RPL. B elements are not kept in
-// registers between the inner products and the rotation (they are read again
-// from shared memory), which leaves the A columns the only long-lived arrays.
-//
-// Schedule: the warps form G independent groups (G divides nmax and the warp
-// count); group g owns A slots g H .. g H + H - 1 (H = nmax / G), two per warp.
-// In phase ph the group meets the B columns of part (g + ph) mod G: in local
-// round r its slot pl meets B column part H + (pl + r) mod H. Every B column is
-// touched by exactly one slot in each global round R = ph H + r, and a slot
-// waits only until its columns have completed round R - 1 (ver[q], acquire /
-// release). G = 1 is one cyclic ring of warps; G > 1 gives G rings that run
-// independently (measured no faster at chi = 128 with two CTAs per SM, so the
-// default is 1).
+// Single-precision cross pass: warp w holds A columns p0 = w and p1 = w + nw in
+// registers for the whole pass and, in round r, takes one B column
+// q = (w + r) mod nbp (nbp = max(nb, warps)). The column is loaded once and
+// meets both A columns in turn: pair (p0, q) first, then (p1, q') with q' the
+// column after the first rotation. The Gram entries of the second pair follow
+// from those of the first without touching the data again:
+//   |q'|^2 = s^2 |a0|^2 + c^2 |q|^2 + 2 s c |a0^H q|,
+//   a1^H q' = s a1^H a0 + c e^{-i phi} a1^H q,
+// which costs one extra inner product (a1^H a0) per round. When the first pair
+// does not rotate, q' = q and the second pair uses the exact inner products, so
+// a sweep that rotates nothing (the convergence test) decides on exact values.
+// Every (A, B) pair is met once per pass. Column q's previous user is warp
+// w + 1 one round earlier, or, for the last warp, warp 0 nbp - nw + 1 rounds
+// earlier: a warp waits (acquire) until that round has released the column.
+// FULL drops the row bounds when m = 32 RPL.
 template <int RPL, bool FULL>
 __device__ __noinline__ void cross_pass_f32(float2* XA, int na, float2* XB, int nb, int m, float tol, float thr,
-                                            int* ver, int* ibuf, int groups) {
+                                            int* ver, int* ibuf) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int nmax = max(na, nb);
-  const int G = (groups > 1 && nmax % groups == 0 && nw % groups == 0) ? groups : 1;
-  const int H = nmax / G, WG = nw / G;
-  const int g = w / WG, wl = w - g * WG;
-  for (int c = threadIdx.x; c < nmax; c += blockDim.x) ver[c] = 0;
+  const int nbp = max(nb, nw);
+  for (int c = threadIdx.x; c < nbp; c += blockDim.x) ver[c] = 0;
   __syncthreads();
-  const int pl0 = wl, pl1 = wl + WG;
-  const bool o0 = pl0 < H, o1 = pl1 < H;  // slots this warp owns
-  const int p0 = g * H + pl0, p1 = g * H + pl1;
-  const bool h0 = o0 && p0 < na, h1 = o1 && p1 < na;
+  const int p0 = w, p1 = w + nw;
+  const bool h0 = p0 < na, h1 = p1 < na;
   const float2 zero = make_float2(0.f, 0.f);
-  float2 a0[RPL], a1[RPL];
+  float2 a0[RPL], a1[RPL], qv[RPL];
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     const int row = lane + 32 * t;
@@ -275,86 +269,80 @@ __device__ __noinline__ void cross_pass_f32(float2* XA, int na, float2* XB, int 
     a0[t] = (h0 && in) ? XA[(size_t)p0 * m + row] : zero;
     a1[t] = (h1 && in) ? XA[(size_t)p1 * m + row] : zero;
   }
-  auto wait = [&](const int* vp, int r) {
-    for (int it = 0; handoff::ld_acquire(vp) < r; ++it) {
+  auto wait = [&](const int* vp, int need) {
+    for (int it = 0; handoff::ld_acquire(vp) < need; ++it) {
       if (it >= (1 << 22) || ibuf[5]) { ibuf[5] = 1; return; }
     }
   };
+  const int gap = nbp - nw;
   int rot = 0, chk = 0;
-  for (int ph = 0; ph < G && o0; ++ph) {
-    const int part = (g + ph) % G;
-    int lq0 = pl0, lq1 = pl1 < H ? pl1 : 0;
-    for (int r = 0; r < H; ++r) {
-      const int R = ph * H + r;
-      const int q0 = part * H + lq0, q1 = part * H + lq1;
-      wait(ver + q0, R);
-      if (o1) wait(ver + q1, R);
-      const bool d0 = h0 && q0 < nb, d1 = h1 && q1 < nb;
-      chk += (int)d0 + (int)d1;
-      float2* xb0 = XB + (size_t)q0 * m;
-      float2* xb1 = XB + (size_t)q1 * m;
-      float2 aa0 = zero, bb0 = zero, ab0 = zero, ax0 = zero, aa1 = zero, bb1 = zero, ab1 = zero, ax1 = zero;
+  int q = w;
+  for (int r = 0; r < nbp; ++r) {
+    const int prev = (w + 1 < nw) ? r - 1 : r - 1 - gap;
+    if (prev >= 0) wait(ver + q, prev + 1);
+    const bool dq = q < nb;
+    chk += (int)(dq && h0) + (int)(dq && h1);
+    float2* xq = XB + (size_t)q * m;
+    float al0 = 0, al1 = 0, be = 0, gr0 = 0, gi0 = 0, gr1 = 0, gi1 = 0, cr = 0, ci = 0;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int row = lane + 32 * t;
+      qv[t] = (dq && (FULL || row < m)) ? xq[row] : zero;
+      const float2 u0 = a0[t], u1 = a1[t], vv = qv[t];
+      al0 = fmaf(u0.x, u0.x, fmaf(u0.y, u0.y, al0));
+      al1 = fmaf(u1.x, u1.x, fmaf(u1.y, u1.y, al1));
+      be = fmaf(vv.x, vv.x, fmaf(vv.y, vv.y, be));
+      gr0 = fmaf(u0.x, vv.x, fmaf(u0.y, vv.y, gr0));
+      gi0 = fmaf(u0.x, vv.y, fmaf(-u0.y, vv.x, gi0));
+      gr1 = fmaf(u1.x, vv.x, fmaf(u1.y, vv.y, gr1));
+      gi1 = fmaf(u1.x, vv.y, fmaf(-u1.y, vv.x, gi1));
+      cr = fmaf(u1.x, u0.x, fmaf(u1.y, u0.y, cr));
+      ci = fmaf(u1.x, u0.y, fmaf(-u1.y, u0.x, ci));
+    }
+    float v8[8] = {al0, al1, be, gr0, gi0, gr1, gi1, cr};
+    warp_sum8<float>(v8, lane);
+    ci = warp_sum(ci);
+    al0 = v8[0]; al1 = v8[1]; be = v8[2]; gr0 = v8[3]; gi0 = v8[4]; gr1 = v8[5]; gi1 = v8[6]; cr = v8[7];
+    float c0, s0, er0, ei0, c1, s1, er1, ei1;
+    const bool r0 = dq && h0 && rot_params<float>(al0, be, gr0, gi0, tol, thr, c0, s0, er0, ei0);
+    if (r0) {
+      const float g0 = sqrtf(fmaf(gr0, gr0, gi0 * gi0));
+      const float ngr = s0 * cr + c0 * (er0 * gr1 - ei0 * gi1);
+      const float ngi = s0 * ci + c0 * (er0 * gi1 + ei0 * gr1);
+      be = s0 * s0 * al0 + c0 * c0 * be + 2.f * s0 * c0 * g0;
+      gr1 = ngr;
+      gi1 = ngi;
+      // w = e^{-i phi} q; a0 <- c a0 - s w; q <- s a0 + c w
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const float2 vv = qv[t], u = a0[t];
+        const float wx = er0 * vv.x - ei0 * vv.y, wy = er0 * vv.y + ei0 * vv.x;
+        a0[t] = make_float2(c0 * u.x - s0 * wx, c0 * u.y - s0 * wy);
+        qv[t] = make_float2(s0 * u.x + c0 * wx, s0 * u.y + c0 * wy);
+      }
+      ++rot;
+    }
+    const bool r1 = dq && h1 && rot_params<float>(al1, be, gr1, gi1, tol, thr, c1, s1, er1, ei1);
+    if (r1) {
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const float2 vv = qv[t], u = a1[t];
+        const float wx = er1 * vv.x - ei1 * vv.y, wy = er1 * vv.y + ei1 * vv.x;
+        a1[t] = make_float2(c1 * u.x - s1 * wx, c1 * u.y - s1 * wy);
+        qv[t] = make_float2(s1 * u.x + c1 * wx, s1 * u.y + c1 * wy);
+      }
+      ++rot;
+    }
+    if (r0 || r1) {
 #pragma unroll
       for (int t = 0; t < RPL; ++t) {
         const int row = lane + 32 * t;
-        const bool in = FULL || row < m;
-        const float2 b0 = (d0 && in) ? xb0[row] : zero;
-        const float2 b1 = (d1 && in) ? xb1[row] : zero;
-        aa0 = __ffma2_rn(a0[t], a0[t], aa0);
-        bb0 = __ffma2_rn(b0, b0, bb0);
-        ab0 = __ffma2_rn(a0[t], b0, ab0);
-        ax0 = __ffma2_rn(a0[t], make_float2(b0.y, b0.x), ax0);
-        aa1 = __ffma2_rn(a1[t], a1[t], aa1);
-        bb1 = __ffma2_rn(b1, b1, bb1);
-        ab1 = __ffma2_rn(a1[t], b1, ab1);
-        ax1 = __ffma2_rn(a1[t], make_float2(b1.y, b1.x), ax1);
+        if (FULL || row < m) xq[row] = qv[t];
       }
-      // al = |a|^2, be = |b|^2, gr + i gi = a^H b
-      float v8[8] = {aa0.x + aa0.y, bb0.x + bb0.y, ab0.x + ab0.y, ax0.x - ax0.y,
-                     aa1.x + aa1.y, bb1.x + bb1.y, ab1.x + ab1.y, ax1.x - ax1.y};
-      warp_sum8<float>(v8, lane);
-      float c0, s0, er0, ei0, c1, s1, er1, ei1;
-      const bool r0 = d0 && rot_params<float>(v8[0], v8[1], v8[2], v8[3], tol, thr, c0, s0, er0, ei0);
-      const bool r1 = d1 && rot_params<float>(v8[4], v8[5], v8[6], v8[7], tol, thr, c1, s1, er1, ei1);
-      if (r0) {
-        // w = e^{-i phi} b; a <- c a - s w; b <- s a + c w
-        const float2 e1 = make_float2(er0, er0), e2 = make_float2(-ei0, ei0);
-        const float2 cc = make_float2(c0, c0), ss = make_float2(s0, s0), ns = make_float2(-s0, -s0);
-#pragma unroll
-        for (int t = 0; t < RPL; ++t) {
-          const int row = lane + 32 * t;
-          if (!(FULL || row < m)) continue;
-          const float2 b = xb0[row];
-          const float2 wv = __ffma2_rn(e1, b, __fmul2_rn(e2, make_float2(b.y, b.x)));
-          const float2 u = a0[t];
-          a0[t] = __ffma2_rn(cc, u, __fmul2_rn(ns, wv));
-          xb0[row] = __ffma2_rn(ss, u, __fmul2_rn(cc, wv));
-        }
-        ++rot;
-      }
-      if (r1) {
-        const float2 e1 = make_float2(er1, er1), e2 = make_float2(-ei1, ei1);
-        const float2 cc = make_float2(c1, c1), ss = make_float2(s1, s1), ns = make_float2(-s1, -s1);
-#pragma unroll
-        for (int t = 0; t < RPL; ++t) {
-          const int row = lane + 32 * t;
-          if (!(FULL || row < m)) continue;
-          const float2 b = xb1[row];
-          const float2 wv = __ffma2_rn(e1, b, __fmul2_rn(e2, make_float2(b.y, b.x)));
-          const float2 u = a1[t];
-          a1[t] = __ffma2_rn(cc, u, __fmul2_rn(ns, wv));
-          xb1[row] = __ffma2_rn(ss, u, __fmul2_rn(cc, wv));
-        }
-        ++rot;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        handoff::st_release(ver + q0, R + 1);
-        if (o1) handoff::st_release(ver + q1, R + 1);
-      }
-      lq0 = lq0 + 1 == H ? 0 : lq0 + 1;
-      lq1 = lq1 + 1 == H ? 0 : lq1 + 1;
     }
+    __syncwarp();
+    if (lane == 0) handoff::st_release(ver + q, r + 1);
+    q = q + 1 == nbp ? 0 : q + 1;
   }
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
@@ -378,11 +366,12 @@ __device__ __noinline__ void cross_pass_f32(float2* XA, int na, float2* XB, int 
 template <typename R>
 template <int RPL>
 __device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
-  if constexpr (sizeof(R) == 4) {
+  // the column counters live in sm.perm (2 cap entries)
+  if constexpr (sizeof(R) == 4) if (max(nb, (int)(nt() >> 5)) <= 2 * cap) {
     float2* xa = reinterpret_cast<float2*>(XA);
     float2* xb = reinterpret_cast<float2*>(XB);
-    if (m == 32 * RPL) cross_pass_f32<RPL, true>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf, a.jac_groups);
-    else cross_pass_f32<RPL, false>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf, a.jac_groups);
+    if (m == 32 * RPL) cross_pass_f32<RPL, true>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf);
+    else cross_pass_f32<RPL, false>(xa, na, xb, nb, m, tol, thr, sm.perm, sm.ibuf);
     return;
   }
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
