@@ -249,18 +249,21 @@ __device__ __noinline__ void Engine<R>::panel_t(const C* V, int m, int j0, int b
     if (lane == 0) T[k * 16 + jj] = C{sr, si};
   }
   __syncthreads();
-  if (tid() == 0) {
+  // Column jj needs the finished columns < jj of T and the raw z column jj, so
+  // one warp forms it with lane k computing row k; the sum over q runs in the
+  // same order as a serial loop would take it.
+  if (w == 0) {
+    const int k = lane;
     for (int jj = 0; jj < bp; ++jj) {
       const R tj = tau[j0 + jj].re;
-      C tmp[16];
-      for (int k = 0; k < jj; ++k) {
-        C acc = {0, 0};
+      C acc = {0, 0};
+      if (k < jj)
         for (int q = k; q < jj; ++q) fma_c(acc, T[k * 16 + q], T[q * 16 + jj]);
-        tmp[k] = C{-tj * acc.re, -tj * acc.im};
-      }
-      for (int k = 0; k < jj; ++k) T[k * 16 + jj] = tmp[k];
-      T[jj * 16 + jj] = C{tj, 0};
-      for (int k = jj + 1; k < 16; ++k) T[k * 16 + jj] = C{0, 0};
+      __syncwarp();
+      if (k < jj) T[k * 16 + jj] = C{-tj * acc.re, -tj * acc.im};
+      else if (k == jj) T[k * 16 + jj] = C{tj, 0};
+      else if (k < 16) T[k * 16 + jj] = C{0, 0};
+      __syncwarp();
     }
   }
   __syncthreads();
