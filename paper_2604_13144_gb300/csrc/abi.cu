@@ -11,6 +11,8 @@
 namespace tepai {
 cudaError_t launch_ensemble_f32(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_ensemble_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_canon_f32(const KArgs& a, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_canon_f64(const KArgs& a, int block, size_t smem, cudaStream_t st);
 cudaError_t occupancy_ensemble_f32(int block, size_t smem, int* ctas_per_sm);
 cudaError_t occupancy_ensemble_f64(int block, size_t smem, int* ctas_per_sm);
 cudaError_t launch_signed_reduce(const double* v, const signed char* sign, long long ns, int M, int nobs,
@@ -51,7 +53,8 @@ int jacobi_precondition() {
 }
 
 struct Layout {
-  size_t terms, snaps, gnorm, obs, bits, dims, init, stats, counter, status, v, sign, arena, stride, total;
+  size_t terms, snaps, gnorm, obs, bits, dims, init, canon_meta, stats, counter, status, v, sign, arena, stride,
+      canon, total;
 };
 
 Layout layout(const HostPlan& hp, const tepai_params* Q, int grid, bool has_init, size_t init_elems) {
@@ -73,6 +76,9 @@ Layout layout(const HostPlan& hp, const tepai_params* Q, int grid, bool has_init
   L.sign = o; o = al256(o + (size_t)Q->n_samples * hp.M);
   L.stride = al256(((size_t)hp.n * 2 * cap * cap + 8 * cap * cap) * nc.csize);
   L.arena = o; o = al256(o + L.stride * (size_t)grid);
+  // one more arena slot for the canonical form of a shared start state
+  L.canon = o; o = al256(o + (has_init ? L.stride : 0));
+  L.canon_meta = o; o = al256(o + (has_init ? sizeof(int) * (hp.n + 2) : 0));
   L.total = o;
   return L;
 }
@@ -169,6 +175,18 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   a.status = reinterpret_cast<int*>(base + L.status);
   a.x_in_smem = ls.x_in_smem; a.smem_x_elems = ls.x_elems;
   a.precondition = jacobi_precondition();
+  if (init) {
+    // bring the shared start state to canonical form once; every sample copies it
+    a.canon = base + L.canon;
+    a.canon_meta = reinterpret_cast<int*>(base + L.canon_meta);
+    CK(cudaMemsetAsync(a.status, 0, 4 * sizeof(int), st));
+    CK(Q->precision == TEPAI_FP64 ? launch_canon_f64(a, ls.block, ls.smem, st)
+                                  : launch_canon_f32(a, ls.block, ls.smem, st));
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, a.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (status != 0) return TEPAI_ERR_DEVICE_CHECK;
+  }
   pr.precision = Q->precision; pr.grid = ls.grid; pr.block = ls.block; pr.smem = ls.smem;
   pr.n_samples = Q->n_samples; pr.M = hp.M; pr.n_obs = hp.n_obs;
   pr.gnorm = reinterpret_cast<double*>(base + L.gnorm);

@@ -89,6 +89,8 @@ struct KArgs {
   const int* snaps;          // [M] snapshot steps
   const int* obs;            // [n_obs]
   const int* init_dims;      // [n+1] or nullptr
+  const char* canon;         // arena slot holding the start state in canonical form, or nullptr
+  int* canon_meta;           // [n+2]: its bond dimensions, then its centre
   const double* init_tensors;// complex interleaved FP64, or nullptr
   const unsigned char* init_bits;  // [n]
   char* arena;               // per-CTA arena base

@@ -340,6 +340,7 @@ struct Engine {
   // state preparation
   __device__ void init_product();
   __device__ void init_from_tensors();
+  __device__ void init_from_canonical();
   __device__ void normalise_centre();
   // single-site unitary u (2x2 row-major) on site i
   __device__ void apply_1site(int i, const C u[4]);

@@ -11,6 +11,13 @@ cudaError_t launch_ensemble_f32(const KArgs& a, int grid, int block, size_t smem
   return cudaGetLastError();
 }
 
+cudaError_t launch_canon_f32(const KArgs& a, int block, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(canon_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  canon_kernel<float><<<1, block, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t occupancy_ensemble_f32(int block, size_t smem, int* ctas_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(ensemble_kernel<float>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -48,6 +48,33 @@ __device__ __noinline__ void Engine<R>::init_from_tensors() {
   }
 }
 
+// Start from the canonical form that canon_kernel left in a.canon: bond
+// dimensions, centre and site tensors are copied (16-byte vectors; every site
+// slot starts 16-byte aligned and holds a multiple of 16 bytes when the
+// dimensions are even, else the tail is copied element-wise).
+template <typename R>
+__device__ __noinline__ void Engine<R>::init_from_canonical() {
+  for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = a.canon_meta[i];
+  __syncthreads();
+  for (int i = 0; i <= a.n; ++i)
+    if (!dim_ok(sm.dims[i])) { fail(ST_BAD_DIM, 7500 + i); return; }
+  const C* src0 = reinterpret_cast<const C*>(a.canon);
+  for (int i = 0; i < a.n; ++i) {
+    const size_t cnt = (size_t)sm.dims[i] * 2 * sm.dims[i + 1];
+    const size_t bytes = cnt * sizeof(C);
+    const float4* s4 = reinterpret_cast<const float4*>(src0 + (size_t)i * slot);
+    float4* d4 = reinterpret_cast<float4*>(S(i));
+    for (size_t e = tid(); e < bytes / 16; e += nt()) d4[e] = s4[e];
+    if (bytes % 16 && tid() == 0) {
+      const C* s = src0 + (size_t)i * slot;
+      for (size_t e = (bytes / 16) * 16 / sizeof(C); e < cnt; ++e) S(i)[e] = s[e];
+    }
+  }
+  centre = a.canon_meta[a.n + 1];
+  if (centre < 0 || centre >= a.n) { fail(ST_BAD_DIM, 7600); return; }
+  __syncthreads();
+}
+
 // Rescale the centre tensor (and so the state) to unit norm.
 template <typename R>
 __device__ __noinline__ void Engine<R>::normalise_centre() {
@@ -333,7 +360,9 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
     const unsigned long long s = (unsigned long long)(a.sample_offset + si);
     {
       PhaseTimer pt(eng.st, PH_INIT);
-      if (a.init_tensors) eng.init_from_tensors(); else eng.init_product();
+      if (a.canon) eng.init_from_canonical();
+      else if (a.init_tensors) eng.init_from_tensors();
+      else eng.init_product();
     }
     int sign_count = 0;
     int mi = 0;
@@ -372,6 +401,28 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
     atomicAdd(&a.stats->jac_pairs, st.jac_pairs);
     atomicAdd(&a.stats->jac_rots, st.jac_rots);
     for (int p = 0; p < SP_N; ++p) atomicAdd(&a.stats->sub_cycles[p], st.sub_cycles[p]);
+  }
+}
+
+// The canonical form of a shared start state, computed once per prepared
+// problem by one CTA: the same steps as init_from_tensors in every sample
+// (right-canonical, centre on site 0, unit norm), written to the arena slot
+// a.canon with its bond dimensions and centre in a.canon_meta.
+template <typename R>
+__global__ void __launch_bounds__(512, 1) canon_kernel(const __grid_constant__ KArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SmemLayout sm = carve_smem(smem_raw, a, (int)sizeof(cplx<R>));
+  Engine<R> eng(a, sm, const_cast<char*>(a.canon));
+  if (threadIdx.x == 0) {
+    sm.ibuf[13] = 0; sm.ibuf[14] = 0; sm.ibuf[15] = 0;
+    for (int b = 0; b < 3; ++b) bulk::mbar_init(sm.mbar + b);
+  }
+  __syncthreads();
+  eng.init_from_tensors();
+  __syncthreads();
+  if (threadIdx.x == 0 && !eng.failed()) {
+    for (int i = 0; i <= a.n; ++i) a.canon_meta[i] = sm.dims[i];
+    a.canon_meta[a.n + 1] = eng.centre;
   }
 }
 
