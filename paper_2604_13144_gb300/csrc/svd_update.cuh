@@ -165,6 +165,102 @@ __device__ __forceinline__ bool rotate_pair_m(cplx<R>* xp, cplx<R>* xq, int m, R
   return rotate_pair<R, 16>(xp, xq, m, tol, thr, lane);
 }
 
+// Single-precision round-robin pass with two slots per warp processed together
+// (slots w and w + nw of every round): the four columns are loaded, the eight
+// Gram sums share one warp reduction, and both rotations run before the
+// columns are stored and released. Same schedule, handoff and rotation rule as
+// Engine::rr_pass; FULL drops the row bounds when m = 32 RPL.
+template <int RPL, bool FULL>
+__device__ __noinline__ void rr_pass_f32(float2* X, int m, int nc, float tol, float thr, int* ver, int* ibuf) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int np = nc + (nc & 1), half = np / 2;
+  for (int c = threadIdx.x; c < np; c += blockDim.x) ver[c] = 0;
+  __syncthreads();
+  const int t0 = w, t1 = w + nw;
+  const bool o0 = t0 < half, o1 = t1 < half;
+  const float2 zero = make_float2(0.f, 0.f);
+  auto wait = [&](const int* vp, int need) {
+    for (int it = 0; handoff::ld_acquire(vp) < need; ++it) {
+      if (it >= (1 << 22) || ibuf[5]) { ibuf[5] = 1; return; }
+    }
+  };
+  auto slot = [&](int t, int r, int& p, int& q) {
+    if (t == 0) { p = np - 1; q = r; }
+    else { p = (r + t) % (np - 1); q = (r - t + np - 1) % (np - 1); }
+  };
+  int rot = 0, chk = 0;
+  for (int r = 0; r < np - 1 && o0; ++r) {
+    int p0, q0, p1 = 0, q1 = 0;
+    slot(t0, r, p0, q0);
+    if (o1) slot(t1, r, p1, q1);
+    wait(ver + p0, r);
+    wait(ver + q0, r);
+    if (o1) { wait(ver + p1, r); wait(ver + q1, r); }
+    const bool d0 = p0 < nc && q0 < nc, d1 = o1 && p1 < nc && q1 < nc;
+    chk += (int)d0 + (int)d1;
+    float2* xp0 = X + (size_t)p0 * m;
+    float2* xq0 = X + (size_t)q0 * m;
+    float2* xp1 = X + (size_t)p1 * m;
+    float2* xq1 = X + (size_t)q1 * m;
+    float2 u0[RPL], v0[RPL], u1[RPL], v1[RPL];
+    float al0 = 0, be0 = 0, gr0 = 0, gi0 = 0, al1 = 0, be1 = 0, gr1 = 0, gi1 = 0;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int row = lane + 32 * t;
+      const bool in = FULL || row < m;
+      u0[t] = (d0 && in) ? xp0[row] : zero;
+      v0[t] = (d0 && in) ? xq0[row] : zero;
+      u1[t] = (d1 && in) ? xp1[row] : zero;
+      v1[t] = (d1 && in) ? xq1[row] : zero;
+      al0 = fmaf(u0[t].x, u0[t].x, fmaf(u0[t].y, u0[t].y, al0));
+      be0 = fmaf(v0[t].x, v0[t].x, fmaf(v0[t].y, v0[t].y, be0));
+      gr0 = fmaf(u0[t].x, v0[t].x, fmaf(u0[t].y, v0[t].y, gr0));
+      gi0 = fmaf(u0[t].x, v0[t].y, fmaf(-u0[t].y, v0[t].x, gi0));
+      al1 = fmaf(u1[t].x, u1[t].x, fmaf(u1[t].y, u1[t].y, al1));
+      be1 = fmaf(v1[t].x, v1[t].x, fmaf(v1[t].y, v1[t].y, be1));
+      gr1 = fmaf(u1[t].x, v1[t].x, fmaf(u1[t].y, v1[t].y, gr1));
+      gi1 = fmaf(u1[t].x, v1[t].y, fmaf(-u1[t].y, v1[t].x, gi1));
+    }
+    float v8[8] = {al0, be0, gr0, gi0, al1, be1, gr1, gi1};
+    warp_sum8<float>(v8, lane);
+    float c0, s0, er0, ei0, c1, s1, er1, ei1;
+    const bool r0 = d0 && rot_params<float>(v8[0], v8[1], v8[2], v8[3], tol, thr, c0, s0, er0, ei0);
+    const bool r1 = d1 && rot_params<float>(v8[4], v8[5], v8[6], v8[7], tol, thr, c1, s1, er1, ei1);
+    if (r0) {
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int row = lane + 32 * t;
+        if (!(FULL || row < m)) continue;
+        const float2 vv = v0[t], u = u0[t];
+        const float wx = er0 * vv.x - ei0 * vv.y, wy = er0 * vv.y + ei0 * vv.x;
+        xp0[row] = make_float2(c0 * u.x - s0 * wx, c0 * u.y - s0 * wy);
+        xq0[row] = make_float2(s0 * u.x + c0 * wx, s0 * u.y + c0 * wy);
+      }
+      ++rot;
+    }
+    if (r1) {
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int row = lane + 32 * t;
+        if (!(FULL || row < m)) continue;
+        const float2 vv = v1[t], u = u1[t];
+        const float wx = er1 * vv.x - ei1 * vv.y, wy = er1 * vv.y + ei1 * vv.x;
+        xp1[row] = make_float2(c1 * u.x - s1 * wx, c1 * u.y - s1 * wy);
+        xq1[row] = make_float2(s1 * u.x + c1 * wx, s1 * u.y + c1 * wy);
+      }
+      ++rot;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      handoff::st_release(ver + p0, r + 1);
+      handoff::st_release(ver + q0, r + 1);
+      if (o1) { handoff::st_release(ver + p1, r + 1); handoff::st_release(ver + q1, r + 1); }
+    }
+  }
+  if (lane == 0) { if (rot) atomicAdd(&ibuf[0], rot); if (chk) atomicAdd(&ibuf[6], chk); }
+  __syncthreads();
+}
+
 // One cyclic pass over all pairs of the nc columns of X (m rows, column-major)
 // in parallel round-robin order (Brent & Luk, SIAM J. Sci. Stat. Comput. 6,
 // 1985): np-1 rounds of disjoint pairs (np = nc rounded up to even), slot t
@@ -177,6 +273,16 @@ __device__ __forceinline__ bool rotate_pair_m(cplx<R>* xp, cplx<R>* xq, int m, R
 // counted in ibuf[0].
 template <typename R>
 __device__ __noinline__ void Engine<R>::rr_pass(C* X, int m, int nc, R tol, R thr) {
+  if constexpr (sizeof(R) == 4) if (m <= 256 && nc + (nc & 1) <= 2 * cap) {
+    float2* xf = reinterpret_cast<float2*>(X);
+    if (m <= 64) { if (m == 64) rr_pass_f32<2, true>(xf, m, nc, tol, thr, sm.perm, sm.ibuf);
+                   else rr_pass_f32<2, false>(xf, m, nc, tol, thr, sm.perm, sm.ibuf); }
+    else if (m <= 128) { if (m == 128) rr_pass_f32<4, true>(xf, m, nc, tol, thr, sm.perm, sm.ibuf);
+                         else rr_pass_f32<4, false>(xf, m, nc, tol, thr, sm.perm, sm.ibuf); }
+    else { if (m == 256) rr_pass_f32<8, true>(xf, m, nc, tol, thr, sm.perm, sm.ibuf);
+           else rr_pass_f32<8, false>(xf, m, nc, tol, thr, sm.perm, sm.ibuf); }
+    return;
+  }
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int np = nc + (nc & 1);
   int* ver = sm.perm;
@@ -538,17 +644,12 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
   C* xs = reinterpret_cast<C*>(sm.x);
   // column blocks of bw: the width the staging buffer allows, at most 2 columns
   // per warp so that a block's warp-owned columns fit in registers
-  // Staged blocks: two (I, J) or, when that costs no block width, three (I and
-  // a double-buffered J whose next load overlaps the cross pass).
+  // Staged blocks: two (I and J) fit in the staging room. (A third block for
+  // double-buffered loads of J measured no faster with two CTAs per SM, whose
+  // co-resident CTA already covers the copy latency.)
   int bw = 1;
-  bool prefetch = false;
   if (!x_in_smem) {
-    int bw3 = 1;
     while (4 * bw * m <= a.smem_x_elems && 2 * bw < nc) bw *= 2;
-    while (6 * bw3 * m <= a.smem_x_elems && 2 * bw3 < nc) bw3 *= 2;
-    if (bw > 2 * nw) bw = 2 * nw;
-    if (bw3 > 2 * nw) bw3 = 2 * nw;
-    prefetch = bw3 >= bw;
   } else {
     bw = nc;
   }
@@ -571,17 +672,31 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
         rr_pass(xI, m, nI, tol, thr);
         for (int J = I + 1; J < nbk; ++J) cross(xI, nI, X + (size_t)J * bw * m, min(bw, nc - J * bw));
       }
-    } else if (!prefetch) {
-      // blocks are contiguous column ranges of X: whole-block bulk copies
+    } else {
+      // Blocks are contiguous column ranges of X, moved by whole-block bulk
+      // copies into sa (block I) and sb (block J), which are adjacent in
+      // shared memory. Blocks 2k and 2k+1 form a super-block: one round-robin
+      // pass over its 2 bw columns covers the pairs inside both blocks and
+      // those between them, with two pairs per warp in every round. Every pair
+      // of columns is still visited exactly once per sweep.
       C* sa = xs;
       C* sb = xs + (size_t)bw * m;
       for (int I = 0; I < nbk && !failed(); ++I) {
         const int nI = min(bw, nc - I * bw);
         C* gI = X + (size_t)I * bw * m;
+        const bool lead = (I % 2 == 0) && (I + 1 < nbk);
         bulk_load(sa, gI, (uint32_t)(sizeof(C) * nI * m));
         if (failed()) break;
-        rr_pass(sa, m, nI, tol, thr);
-        for (int J = I + 1; J < nbk; ++J) {
+        if (lead) {
+          const int n1 = min(bw, nc - (I + 1) * bw);
+          bulk_load(sb, gI + (size_t)bw * m, (uint32_t)(sizeof(C) * n1 * m));
+          if (failed()) break;
+          rr_pass(xs, m, nI + n1, tol, thr);
+          bulk_store(gI + (size_t)bw * m, sb, (uint32_t)(sizeof(C) * n1 * m));
+        } else if (I % 2 == 0) {
+          rr_pass(sa, m, nI, tol, thr);
+        }
+        for (int J = lead ? I + 2 : I + 1; J < nbk; ++J) {
           const int nJ = min(bw, nc - J * bw);
           C* gJ = X + (size_t)J * bw * m;
           bulk_load(sb, gJ, (uint32_t)(sizeof(C) * nJ * m));
@@ -591,48 +706,6 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
         }
         bulk_store(gI, sa, (uint32_t)(sizeof(C) * nI * m));
       }
-    } else {
-      // Blocks are contiguous column ranges of X, moved by whole-block bulk
-      // copies: block I in sa, blocks J double-buffered in sb[0] / sb[1]. The
-      // load of J+1 runs during the cross pass of J; stores complete in the
-      // background and are drained before any block is read back.
-      C* sa = xs;
-      C* sb[2] = {xs + (size_t)bw * m, xs + (size_t)2 * bw * m};
-      auto bytes_of = [&](int blk) { return (uint32_t)(sizeof(C) * min(bw, nc - blk * bw) * m); };
-      int pend = 0;  // load slots in flight
-      for (int I = 0; I < nbk && !failed(); ++I) {
-        const int nI = min(bw, nc - I * bw);
-        C* gI = X + (size_t)I * bw * m;
-        bulk_drain();
-        bulk_issue_load(0, sa, gI, bytes_of(I));
-        pend |= 1;
-        if (I + 1 < nbk) { bulk_issue_load(1, sb[0], gI + (size_t)bw * m, bytes_of(I + 1)); pend |= 2; }
-        bulk_wait_load(0, bytes_of(I));
-        pend &= ~1;
-        if (failed()) break;
-        rr_pass(sa, m, nI, tol, thr);
-        for (int J = I + 1; J < nbk; ++J) {
-          const int b = (J - I - 1) & 1;
-          const int nJ = min(bw, nc - J * bw);
-          C* gJ = X + (size_t)J * bw * m;
-          if (J + 1 < nbk) {
-            bulk_wait_store_read();  // the store of block J-1 has read sb[b^1]
-            bulk_issue_load(1 + (b ^ 1), sb[b ^ 1], gJ + (size_t)bw * m, bytes_of(J + 1));
-            pend |= 2 << (b ^ 1);
-          }
-          bulk_wait_load(1 + b, bytes_of(J));
-          pend &= ~(2 << b);
-          if (failed()) break;
-          cross(sa, nI, sb[b], nJ);
-          bulk_issue_store(gJ, sb[b], bytes_of(J));
-        }
-        if (failed()) break;
-        bulk_issue_store(gI, sa, bytes_of(I));
-      }
-      // a failed wait leaves other loads in flight: let them land before the
-      // CTA gives up its shared memory
-      if (failed()) bulk_settle(pend);
-      bulk_drain();
     }
     ++sweep;
     if (failed()) break;
