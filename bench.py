@@ -29,6 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TE-PAI MPS gate-updates/s at chi=128"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one ensemble_kernel
+# launch of the default workload, divided by the two-site updates of that launch
+# (3.636e12 B over 63089 updates), from one ncu capture of the current kernel.
+DRAM_BYTES_PER_UPDATE = 5.763e7
 UNIT = "updates/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -315,7 +319,9 @@ def run_ours(a):
         "gpu_launches": 2 * a.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (DRAM_BYTES_PER_UPDATE * upd / a.steps
+                                 if (n, par.chi_max, a.window) == (64, 128, 2) else None),
                      "peak_note": "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"},
         "stats": {"events_per_s": events / elapsed, "updates": upd, "alg_flops": flops,
                   "sweeps_per_svd": sweeps / max(upd, 1.0),
