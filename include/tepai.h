@@ -85,6 +85,10 @@ typedef struct {
     unsigned long long seed;       /* Philox4x64-10 key word 0 (key word 1 = global sample index) */
     int variant;                   /* TEPAI_UNBIASED | TEPAI_NO_PI | TEPAI_TROTTER */
     int precision;                 /* TEPAI_FP64 | TEPAI_MIXED */
+    int launch_variant;            /* 0 = built-in launch-shape rule; 1 = two 256-thread CTAs per SM,
+                                      2 = one 512-thread CTA per SM (shapes whose SVD working matrix
+                                      is staged from global memory; otherwise ignored). The value
+                                      tepai_autotune reports is the fastest on this device. */
 } tepai_params;
 
 /* Optional initial MPS shared by all samples (a "hybrid" start). Site tensors
@@ -176,7 +180,12 @@ int tepai_dev_prepare(const tepai_problem *prob, const tepai_params *par, const 
 /* Launch the ensemble on a prepared workspace: kernels only, no host
  * synchronisation, no allocation. Device outputs: d_mean/d_stderr [M][n_obs],
  * d_partials [M][n_obs][3], d_v [n_samples][M][n_obs], d_sign [n_samples][M]
- * (any may be NULL except d_mean). */
+ * (any may be NULL except d_mean). The first call captures its stream work
+ * (counter zeroing, ensemble kernel, reduction, output copies) as a CUDA graph
+ * and later calls replay it; a changed sample offset is written into the
+ * captured kernel's arguments, and other output pointers or another stream
+ * trigger a new capture. Environment TEPAI_GRAPHS=0 launches directly instead.
+ * Calls on one workspace must not overlap. */
 int tepai_dev_execute(void *d_workspace, double *d_mean, double *d_stderr, double *d_partials,
                       double *d_v, signed char *d_sign, void *stream);
 /* Point a prepared workspace at another range of global sample indices
@@ -185,6 +194,21 @@ int tepai_dev_execute(void *d_workspace, double *d_mean, double *d_stderr, doubl
 int tepai_dev_set_sample_offset(void *d_workspace, long long sample_offset);
 /* Copy the device statistics of the last execute on this workspace. Synchronises `stream`. */
 int tepai_dev_stats(void *d_workspace, tepai_stats *stats, void *stream);
+/* Forget a prepared workspace: frees its captured CUDA graph and its
+ * bookkeeping (the caller still owns and frees the device memory). Calling it
+ * on an unknown workspace is a no-op that returns TEPAI_OK. */
+int tepai_dev_release(void *d_workspace);
+
+/* ---- launch-shape autotuner --------------------------------------------
+ * Times every launch variant that applies to this problem on this device (see
+ * tepai_params.launch_variant) on a short trial of the caller's own problem:
+ * the same ring, precision and chi_max, one circuit per CTA, `trial_steps`
+ * Trotter steps (0 = 1) from the given start state. Reports the fastest
+ * variant and its rate in two-site updates per second of kernel time. The
+ * trials use sample indices far above the caller's range and return no
+ * estimates. Uses the context's stream and synchronises it. */
+int tepai_autotune(tepai_ctx *ctx, const tepai_problem *prob, const tepai_params *par,
+                   const tepai_mps *init, long long trial_steps, int *best_variant, double *best_rate);
 
 /* ---- entry point without device allocation ------------------------------
  * The paper has no counterpart: this is a library-usage concern. Some callers

@@ -12,6 +12,12 @@ namespace tepai {
 cudaError_t launch_ensemble_f32(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_ensemble_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_canon_f32(const KArgs& a, int block, size_t smem, cudaStream_t st);
+const void* ensemble_kernel_fn_f32();
+cudaError_t launch_ensemble_captured_f32(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_ensemble_captured_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
+const void* ensemble_kernel_fn_f64();
+cudaError_t set_ensemble_smem_f32(size_t smem);
+cudaError_t set_ensemble_smem_f64(size_t smem);
 cudaError_t launch_canon_f64(const KArgs& a, int block, size_t smem, cudaStream_t st);
 cudaError_t occupancy_ensemble_f32(int block, size_t smem, int* ctas_per_sm);
 cudaError_t occupancy_ensemble_f64(int block, size_t smem, int* ctas_per_sm);
@@ -83,6 +89,37 @@ Layout layout(const HostPlan& hp, const tepai_params* Q, int grid, bool has_init
   return L;
 }
 
+// One execute() captured as a CUDA graph: the zeroing of the counters, the
+// ensemble launch, the reduction and the output copies. It is replayed while
+// the output pointers and the stream stay the same; a new sample offset is
+// written into the captured kernel node's arguments.
+// A default stream (legacy or per-thread) cannot be captured: the graph is
+// then captured on and launched into a stream of its own, ordered after and
+// before the caller's stream by two events.
+struct GraphState {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t kernel = nullptr;
+  const void* outs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t stream = nullptr;     // the caller's stream of the capture
+  cudaStream_t own = nullptr;        // capture / launch stream when the caller's is a default stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  long long offset = -1;
+};
+
+void graph_free(GraphState& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  if (g.own) cudaStreamDestroy(g.own);
+  if (g.ev_in) cudaEventDestroy(g.ev_in);
+  if (g.ev_out) cudaEventDestroy(g.ev_out);
+  g = GraphState{};
+}
+
+bool is_default_stream(cudaStream_t st) {
+  return st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
+}
+
 struct Prepared {
   KArgs ka;
   int precision, grid, block;
@@ -92,7 +129,14 @@ struct Prepared {
   double* gnorm;
   DevStats* stats;
   cudaStream_t stream;
+  GraphState g;
 };
+
+// Graph capture of execute() unless TEPAI_GRAPHS=0.
+bool graphs_enabled() {
+  const char* e = std::getenv("TEPAI_GRAPHS");
+  return !(e && e[0] == '0' && e[1] == 0);
+}
 
 std::mutex g_mu;
 std::unordered_map<void*, Prepared> g_reg;
@@ -108,7 +152,7 @@ int launch_shape(const HostPlan& hp, const tepai_params* Q, int grid_req, Launch
     return Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(block, smem, per_sm)
                                       : occupancy_ensemble_f32(block, smem, per_sm);
   };
-  CK(choose_launch_shape(hp.n, hp.L, Q->chi_max, nc.csize, optin, occ, ls));
+  CK(choose_launch_shape(hp.n, hp.L, Q->chi_max, nc.csize, optin, occ, ls, Q->launch_variant));
   ls.grid = grid_req > 0 ? grid_req : sms * ls.per_sm;
   if (Q->n_samples > 0 && ls.grid > Q->n_samples) ls.grid = (int)Q->n_samples;
   if (ls.grid < 1) ls.grid = 1;
@@ -193,8 +237,82 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   pr.stats = a.stats;
   pr.stream = st;
   std::lock_guard<std::mutex> lk(g_mu);
+  auto old = g_reg.find(ws);
+  if (old != g_reg.end()) graph_free(old->second.g);
   g_reg[ws] = pr;
   return TEPAI_OK;
+}
+
+// The stream work of one execute(): counters zeroed, ensemble launch, reduction, output copies.
+cudaError_t enqueue_execute(const Prepared& pr, double* d_mean, double* d_se, double* d_part, double* d_v,
+                            signed char* d_sign, cudaStream_t st, bool capturing = false) {
+  const KArgs& a = pr.ka;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(a.stats, 0, sizeof(DevStats), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.status, 0, 4 * sizeof(int), st)) != cudaSuccess) return e;
+  if (capturing)
+    e = pr.precision == TEPAI_FP64 ? launch_ensemble_captured_f64(a, pr.grid, pr.block, pr.smem, st)
+                                   : launch_ensemble_captured_f32(a, pr.grid, pr.block, pr.smem, st);
+  else
+    e = pr.precision == TEPAI_FP64 ? launch_ensemble_f64(a, pr.grid, pr.block, pr.smem, st)
+                                   : launch_ensemble_f32(a, pr.grid, pr.block, pr.smem, st);
+  if (e != cudaSuccess) return e;
+  if (d_mean || d_se || d_part)
+    if ((e = launch_signed_reduce(a.v, a.sign, pr.n_samples, pr.M, pr.n_obs, pr.gnorm, d_mean, d_se, d_part, st)) !=
+        cudaSuccess)
+      return e;
+  const size_t nv = (size_t)pr.n_samples * pr.M * pr.n_obs;
+  if (d_v && (e = cudaMemcpyAsync(d_v, a.v, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  if (d_sign &&
+      (e = cudaMemcpyAsync(d_sign, a.sign, (size_t)pr.n_samples * pr.M, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
+// Capture one execute() into pr.g (any earlier graph is freed first).
+cudaError_t capture_execute(Prepared& pr, double* d_mean, double* d_se, double* d_part, double* d_v,
+                            signed char* d_sign, cudaStream_t st) {
+  graph_free(pr.g);
+  // the launch sets the kernel's shared-memory attribute; do it outside the capture
+  cudaError_t e = pr.precision == TEPAI_FP64 ? set_ensemble_smem_f64(pr.smem) : set_ensemble_smem_f32(pr.smem);
+  if (e != cudaSuccess) return e;
+  cudaStream_t cs = st;
+  if (is_default_stream(st)) {
+    if ((e = cudaStreamCreateWithFlags(&pr.g.own, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&pr.g.ev_in, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&pr.g.ev_out, cudaEventDisableTiming)) != cudaSuccess) return e;
+    cs = pr.g.own;
+  }
+  if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+  const cudaError_t eq = enqueue_execute(pr, d_mean, d_se, d_part, d_v, d_sign, cs, true);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  if (eq != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return eq; }
+  if (e != cudaSuccess) return e;
+  const void* fn = pr.precision == TEPAI_FP64 ? ensemble_kernel_fn_f64() : ensemble_kernel_fn_f32();
+  size_t nn = 0;
+  if ((e = cudaGraphGetNodes(graph, nullptr, &nn)) != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn && (e = cudaGraphGetNodes(graph, nodes.data(), &nn)) != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  cudaGraphNode_t kn = nullptr;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams p{};
+    if (cudaGraphKernelNodeGetParams(nd, &p) == cudaSuccess && p.func == fn) kn = nd;
+  }
+  if (!kn) { cudaGraphDestroy(graph); return cudaErrorInvalidValue; }
+  cudaGraphExec_t exec = nullptr;
+  if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  pr.g.graph = graph;
+  pr.g.exec = exec;
+  pr.g.kernel = kn;
+  pr.g.outs[0] = d_mean; pr.g.outs[1] = d_se; pr.g.outs[2] = d_part; pr.g.outs[3] = d_v; pr.g.outs[4] = d_sign;
+  pr.g.stream = st;
+  pr.g.offset = pr.ka.sample_offset;
+  return cudaSuccess;
 }
 
 int execute_impl(void* ws, double* d_mean, double* d_se, double* d_part, double* d_v, signed char* d_sign,
@@ -206,17 +324,46 @@ int execute_impl(void* ws, double* d_mean, double* d_se, double* d_part, double*
     if (it == g_reg.end()) return TEPAI_ERR_INVALID_ARG;
     pr = it->second;
   }
-  const KArgs& a = pr.ka;
-  CK(cudaMemsetAsync(a.stats, 0, sizeof(DevStats), st));
-  CK(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st));
-  CK(cudaMemsetAsync(a.status, 0, 4 * sizeof(int), st));
-  CK(pr.precision == TEPAI_FP64 ? launch_ensemble_f64(a, pr.grid, pr.block, pr.smem, st)
-                                : launch_ensemble_f32(a, pr.grid, pr.block, pr.smem, st));
-  if (d_mean || d_se || d_part)
-    CK(launch_signed_reduce(a.v, a.sign, pr.n_samples, pr.M, pr.n_obs, pr.gnorm, d_mean, d_se, d_part, st));
-  const size_t nv = (size_t)pr.n_samples * pr.M * pr.n_obs;
-  if (d_v) CK(cudaMemcpyAsync(d_v, a.v, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
-  if (d_sign) CK(cudaMemcpyAsync(d_sign, a.sign, (size_t)pr.n_samples * pr.M, cudaMemcpyDeviceToDevice, st));
+  if (!graphs_enabled()) {
+    CK(enqueue_execute(pr, d_mean, d_se, d_part, d_v, d_sign, st));
+    return TEPAI_OK;
+  }
+  const void* want[5] = {d_mean, d_se, d_part, d_v, d_sign};
+  bool same = pr.g.exec && pr.g.stream == st;
+  for (int k = 0; k < 5 && same; ++k) same = pr.g.outs[k] == want[k];
+  if (!same) {
+    const cudaError_t ce = capture_execute(pr, d_mean, d_se, d_part, d_v, d_sign, st);
+    if (ce != cudaSuccess) {
+      graph_free(pr.g);
+      std::lock_guard<std::mutex> lk(g_mu);
+      auto it = g_reg.find(ws);
+      if (it != g_reg.end()) it->second.g = GraphState{};
+      CK(ce);
+    }
+  } else if (pr.g.offset != pr.ka.sample_offset) {
+    cudaKernelNodeParams p{};
+    CK(cudaGraphKernelNodeGetParams(pr.g.kernel, &p));
+    KArgs ka = pr.ka;
+    void* args[1] = {&ka};
+    p.kernelParams = args;
+    p.extra = nullptr;
+    CK(cudaGraphExecKernelNodeSetParams(pr.g.exec, pr.g.kernel, &p));
+    pr.g.offset = pr.ka.sample_offset;
+  }
+  if (pr.g.own) {
+    CK(cudaEventRecord(pr.g.ev_in, st));
+    CK(cudaStreamWaitEvent(pr.g.own, pr.g.ev_in, 0));
+    CK(cudaGraphLaunch(pr.g.exec, pr.g.own));
+    CK(cudaEventRecord(pr.g.ev_out, pr.g.own));
+    CK(cudaStreamWaitEvent(st, pr.g.ev_out, 0));
+  } else {
+    CK(cudaGraphLaunch(pr.g.exec, st));
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_reg.find(ws);
+    if (it != g_reg.end()) it->second.g = pr.g;
+  }
   return TEPAI_OK;
 }
 
@@ -269,7 +416,8 @@ int ctx_reserve(tepai_ctx* c, size_t ws_bytes, size_t out_bytes) {
   if (ws_bytes > c->ws_bytes) {
     if (c->ws) {
       std::lock_guard<std::mutex> lk(g_mu);
-      g_reg.erase(c->ws);
+      auto it = g_reg.find(c->ws);
+    if (it != g_reg.end()) { graph_free(it->second.g); g_reg.erase(it); }
     }
     if (c->ws) CK(cudaFree(c->ws));
     c->ws = nullptr; c->ws_bytes = 0;
@@ -344,7 +492,8 @@ void tepai_destroy(tepai_ctx* c) {
   cudaSetDevice(c->device);
   if (c->ws) {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_reg.erase(c->ws);
+    auto it = g_reg.find(c->ws);
+    if (it != g_reg.end()) { graph_free(it->second.g); g_reg.erase(it); }
   }
   if (c->ws) cudaFree(c->ws);
   if (c->out) cudaFree(c->out);
@@ -376,7 +525,8 @@ int tepai_export_circuit(tepai_ctx* c, const tepai_problem* P, const tepai_param
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_reg.erase(c->ws);
+    auto it = g_reg.find(c->ws);
+    if (it != g_reg.end()) { graph_free(it->second.g); g_reg.erase(it); }
   }
   char* base = static_cast<char*>(c->ws);
   CK(cudaMemcpyAsync(base, hp.terms.data(), sizeof(TermDev) * hp.L, cudaMemcpyHostToDevice, c->stream));
@@ -438,6 +588,81 @@ int tepai_dev_set_sample_offset(void* d_ws, long long sample_offset) {
   auto it = g_reg.find(d_ws);
   if (it == g_reg.end()) return TEPAI_ERR_INVALID_ARG;
   it->second.ka.sample_offset = sample_offset;
+  return TEPAI_OK;
+}
+
+int tepai_dev_release(void* d_ws) {
+  if (!d_ws) return TEPAI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_reg.find(d_ws);
+  if (it != g_reg.end()) {
+    graph_free(it->second.g);
+    g_reg.erase(it);
+  }
+  return TEPAI_OK;
+}
+
+int tepai_autotune(tepai_ctx* c, const tepai_problem* P, const tepai_params* Q, const tepai_mps* init,
+                   long long trial_steps, int* best_variant, double* best_rate) {
+  if (!c || !P || !Q || !best_variant || trial_steps < 0) return TEPAI_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HostPlan hp;
+  int rc = build_plan(P, Q, hp);
+  if (rc) return rc;
+  int best = 0;
+  double best_r = -1.0;
+  LaunchShape seen[3];
+  int n_seen = 0;
+  for (int v = 1; v <= 2; ++v) {
+    tepai_params q = *Q;
+    q.launch_variant = v;
+    q.n_snapshots = 1;
+    q.obs_sites = nullptr;
+    q.n_obs = 0;
+    q.run_steps = trial_steps > 0 ? trial_steps : 1;
+    q.sample_offset = (long long)1 << 40;
+    LaunchShape ls{};
+    rc = launch_shape(hp, &q, 0, ls);
+    if (rc) return rc;
+    bool dup = false;
+    for (int k = 0; k < n_seen; ++k)
+      dup = dup || (seen[k].block == ls.block && seen[k].smem == ls.smem && seen[k].per_sm == ls.per_sm);
+    if (dup) continue;
+    seen[n_seen++] = ls;
+    q.n_samples = ls.grid > 0 ? ls.grid : sms;
+    // prepare (including the one-off canonical start state) outside the timed region
+    size_t ws_bytes = 0;
+    rc = tepai_dev_workspace_size(P, &q, 0, &ws_bytes);
+    if (rc) return rc;
+    const size_t mo = (size_t)hp.M * hp.n_obs;
+    rc = ctx_reserve(c, ws_bytes, sizeof(double) * 5 * mo + 256);
+    if (rc) return rc;
+    rc = prepare_impl(P, &q, init, true, c->ws, c->ws_bytes, 0, c->stream);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, c->stream));
+    rc = execute_impl(c->ws, c->out, nullptr, nullptr, nullptr, nullptr, c->stream);
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    tepai_stats st{};
+    rc = stats_impl(c->ws, &st, c->stream);
+    if (rc) return rc;
+    if (st.device_status[0] != 0) return TEPAI_ERR_DEVICE_CHECK;
+    const double rate = (st.gate_updates + st.swap_updates) / (ms > 0.f ? ms * 1e-3 : 1e-9);
+    if (rate > best_r) { best_r = rate; best = v; }
+  }
+  *best_variant = best;
+  if (best_rate) *best_rate = best_r;
   return TEPAI_OK;
 }
 

@@ -11,6 +11,20 @@ cudaError_t launch_ensemble_f64(const KArgs& a, int grid, int block, size_t smem
   return cudaGetLastError();
 }
 
+// Launch without touching the function attribute (set beforehand), for use
+// inside a CUDA-graph capture.
+cudaError_t launch_ensemble_captured_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
+  ensemble_kernel<double><<<grid, block, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// The kernel's address, to find its node in a captured CUDA graph.
+const void* ensemble_kernel_fn_f64() { return reinterpret_cast<const void*>(ensemble_kernel<double>); }
+
+cudaError_t set_ensemble_smem_f64(size_t smem) {
+  return cudaFuncSetAttribute(ensemble_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 cudaError_t launch_canon_f64(const KArgs& a, int block, size_t smem, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(canon_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -128,6 +128,7 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   if (!(std::isfinite(Q->delta) && Q->delta > 0.0)) return TEPAI_ERR_INVALID_ARG;
   if (Q->chi_max < 1 || !(std::isfinite(Q->cutoff) && Q->cutoff >= 0.0)) return TEPAI_ERR_INVALID_ARG;
   if (Q->variant < 0 || Q->variant > 2 || Q->precision < 0 || Q->precision > 1) return TEPAI_ERR_INVALID_ARG;
+  if (Q->launch_variant < 0 || Q->launch_variant > 2) return TEPAI_ERR_INVALID_ARG;
   if (Q->n_samples < 0 || Q->sample_offset < 0) return TEPAI_ERR_INVALID_ARG;
   const long long S = Q->run_steps ? Q->run_steps : Q->n_steps;
   if (S < 1 || S > Q->n_steps) return TEPAI_ERR_INVALID_ARG;
@@ -225,8 +226,11 @@ struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems, per_s
 // latency and copy-wait stalls, and the modest staging leaves L1 room for
 // the global operands. If two do not fit, one 512-thread CTA per SM stages
 // blocks within 128 KB.
+// `variant` forces one staged shape: 1 = two 256-thread CTAs per SM, 2 = one
+// 512-thread CTA per SM; 0 (or a shape that does not apply) keeps the rule.
 template <class Occ>
-inline cudaError_t choose_launch_shape(int n, int L, int cap, int csize, int optin, Occ occ, LaunchShape& ls) {
+inline cudaError_t choose_launch_shape(int n, int L, int cap, int csize, int optin, Occ occ, LaunchShape& ls,
+                                       int variant = 0) {
   const size_t fixed = smem_fixed_bytes(n, L, cap, csize);
   const size_t xbytes = (size_t)4 * cap * cap * csize;
   int per_sm = 1;
@@ -244,7 +248,7 @@ inline cudaError_t choose_launch_shape(int n, int L, int cap, int csize, int opt
     ls.smem = fixed + (size_t)ls.x_elems * csize;
     e = ls.smem <= (size_t)optin ? occ(ls.block, ls.smem, &per_sm) : cudaSuccess;
     if (e != cudaSuccess) return e;
-    if (ls.smem > (size_t)optin || per_sm < 2) {
+    if (ls.smem > (size_t)optin || (per_sm < 2 && variant != 1) || variant == 2) {
       int bw = 1;
       while ((size_t)2 * (2 * bw) * (2 * cap) * csize <= 131072 && 2 * bw < 2 * cap) bw *= 2;
       ls.block = 512;

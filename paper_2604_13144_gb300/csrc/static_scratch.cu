@@ -92,7 +92,8 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
                                       : occupancy_ensemble_f32(blk, sm_bytes, per);
   };
   LaunchShape ls{};
-  if (choose_launch_shape(hp.n, hp.L, cap, csize, optin, occ, ls) != cudaSuccess) return TEPAI_ERR_CUDA;
+  if (choose_launch_shape(hp.n, hp.L, cap, csize, optin, occ, ls, Q->launch_variant) != cudaSuccess)
+    return TEPAI_ERR_CUDA;
   const int block = ls.block, x_elems = ls.x_elems, x_in_smem = ls.x_in_smem, per_sm = ls.per_sm;
   const size_t smem = ls.smem;
   long long grid = (long long)sms * (per_sm < 1 ? 1 : per_sm);

@@ -21,8 +21,8 @@ TEPAI_FP64, TEPAI_MIXED = 0, 1
 EXPORTED = ["tepai_create", "tepai_destroy", "tepai_run", "tepai_sample_values",
             "tepai_export_circuit", "tepai_gnorm", "tepai_dev_workspace_size",
             "tepai_dev_prepare", "tepai_dev_execute", "tepai_dev_set_sample_offset",
-            "tepai_dev_stats", "tepai_sample_values_static", "tepai_strerror",
-            "tepai_last_cuda_error"]
+            "tepai_dev_stats", "tepai_dev_release", "tepai_autotune", "tepai_sample_values_static",
+            "tepai_strerror", "tepai_last_cuda_error"]
 
 
 class TepaiError(RuntimeError):
@@ -45,7 +45,8 @@ class Params(C.Structure):
                 ("n_samples", C.c_longlong), ("sample_offset", C.c_longlong),
                 ("run_steps", C.c_longlong), ("chi_max", C.c_int), ("cutoff", C.c_double),
                 ("n_snapshots", C.c_int), ("obs_sites", C.POINTER(C.c_int)), ("n_obs", C.c_int),
-                ("seed", C.c_ulonglong), ("variant", C.c_int), ("precision", C.c_int)]
+                ("seed", C.c_ulonglong), ("variant", C.c_int), ("precision", C.c_int),
+                ("launch_variant", C.c_int)]
 
 
 class Mps(C.Structure):
@@ -96,6 +97,8 @@ def _load():
         "tepai_dev_execute": (i, [vp, vp, vp, vp, vp, vp, vp]),
         "tepai_dev_set_sample_offset": (i, [vp, ll]),
         "tepai_dev_stats": (i, [vp, pS, vp]),
+        "tepai_dev_release": (i, [vp]),
+        "tepai_autotune": (i, [vp, pP, pQ, pM, ll, C.POINTER(i), pd]),
         "tepai_sample_values_static": (i, [pP, pQ, vp, vp, vp]),
         "tepai_strerror": (C.c_char_p, [i]),
         "tepai_last_cuda_error": (C.c_char_p, []),
@@ -139,7 +142,7 @@ class Marshalled:
                           int(getattr(par, "sample_offset", 0)), int(getattr(par, "run_steps", 0)),
                           int(par.chi_max), float(par.cutoff), int(par.n_snapshots), obs_p, nobs,
                           int(par.seed) & (2**64 - 1), int(getattr(par, "variant", 0)),
-                          int(getattr(par, "precision", 0)))
+                          int(getattr(par, "precision", 0)), int(getattr(par, "launch_variant", 0)))
         self.n_obs = nobs if obs is not None else int(prob.n)
         self.M = int(par.n_snapshots)
         self.init = None
@@ -209,6 +212,18 @@ def tepai_gnorm(prob, par):
     return g, nu.value
 
 
+def tepai_autotune(ctx, prob, par, init=None, trial_steps: int = 1):
+    """Fastest launch variant for this problem on this device and its rate
+    (two-site updates per second of kernel time); pass the variant as
+    `launch_variant` in later runs."""
+    m = Marshalled(prob, par, init)
+    best, rate = C.c_int(), C.c_double()
+    _check(_lib.tepai_autotune(ctx, C.byref(m.prob), C.byref(m.par),
+                               C.byref(m.init) if m.init is not None else None, int(trial_steps),
+                               C.byref(best), C.byref(rate)), "tepai_autotune")
+    return int(best.value), float(rate.value)
+
+
 class DeviceRun:
     """Device-resident path: the caller's torch tensors hold the workspace and
     the outputs; tepai_dev_execute launches kernels only."""
@@ -253,6 +268,18 @@ class DeviceRun:
         _check(_lib.tepai_dev_stats(C.c_void_p(self.ws.data_ptr()), C.byref(st),
                                     C.c_void_p(self.stream.cuda_stream)), "tepai_dev_stats")
         return st.as_dict()
+
+    def release(self):
+        """Drop the library's bookkeeping and captured graph of this workspace."""
+        if getattr(self, "ws", None) is not None:
+            _lib.tepai_dev_release(C.c_void_p(self.ws.data_ptr()))
+            self.ws = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
 
 
 def tepai_sample_values_static(prob, par, d_v, d_sign, stream=None):

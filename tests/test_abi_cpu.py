@@ -60,6 +60,11 @@ def test_invalid_arguments_are_rejected(T):
     p2.h[3] = float("nan")
     with pytest.raises(T.TepaiError):
         T.tepai_gnorm(p2, par)
+    bad = W.Params(**par.__dict__)
+    bad.launch_variant = 3                                  # variants are 0, 1, 2
+    with pytest.raises(T.TepaiError) as e:
+        T.tepai_gnorm(prob, bad)
+    assert e.value.code == 1
     trot = W.Params(**{**par.__dict__, "n_steps": 100, "variant": 2})   # Trotter has no Delta bound
     g, nu = T.tepai_gnorm(prob, trot)
     assert np.all(g == 1.0) and nu == 100 * 32
