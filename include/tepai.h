@@ -199,6 +199,20 @@ int tepai_dev_stats(void *d_workspace, tepai_stats *stats, void *stream);
  * on an unknown workspace is a no-op that returns TEPAI_OK. */
 int tepai_dev_release(void *d_workspace);
 
+/* Evolve ONE circuit (par->n_samples must be 1; the deterministic Trotter
+ * variant gives the prefix of a hybrid run) from `init` (or the product state)
+ * and return its final MPS in the tepai_mps layout: bond_dims[0..n] and the
+ * site tensors concatenated over chain positions, complex interleaved, FP64,
+ * normalised, in some mixed-canonical gauge. `capacity` is the size of
+ * `tensors` in doubles; n * 2 * chi_max^2 * 2 always suffices. `*used`
+ * receives the doubles written, and TEPAI_ERR_WORKSPACE_TOO_SMALL is returned
+ * (nothing written to tensors) when capacity is short. The result can be
+ * passed as the start state of later runs (Sec. IV hybrid: Trotter to t0,
+ * TE-PAI after). */
+int tepai_evolve_state(tepai_ctx *ctx, const tepai_problem *prob, const tepai_params *par,
+                       const tepai_mps *init, int *bond_dims, double *tensors, long long capacity,
+                       long long *used);
+
 /* ---- launch-shape autotuner --------------------------------------------
  * Times every launch variant that applies to this problem on this device (see
  * tepai_params.launch_variant) on a short trial of the caller's own problem:

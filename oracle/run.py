@@ -20,7 +20,8 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
         floor_rel: float = 1e-14, gap_rel: float = 1e-4, samples=None,
         regauge: bool = False):
     """Return dict with v (Ns, M, n_obs), sign (Ns, M), gnorm (M,), mean,
-    stderr, partials, events_total and per-sample MPS statistics."""
+    stderr, partials, events_total, per-sample MPS statistics and each
+    sample's final MPS (site tensors in chain order; MPS runs only)."""
     plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, par.variant)
     S = par.steps_run()
     snaps = planner.snapshot_steps(S, par.n_snapshots)
@@ -28,7 +29,7 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
            else np.asarray(par.obs_sites, dtype=np.int64))
     idx = (range(par.sample_offset, par.sample_offset + par.n_samples)
            if samples is None else samples)
-    vs, signs, nus, stats = [], [], [], []
+    vs, signs, nus, stats, states = [], [], [], [], []
     for s in idx:
         ev = sampler.sample_events(plan, par.seed, s, S)
         nus.append(len(ev))
@@ -41,6 +42,7 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
             z = mps_mod.run_events(m, plan, ev, snaps, par.chi_max, par.cutoff, floor_rel, gap_rel,
                                    regauge)
             stats.append(m.stats)
+            states.append([a.copy() for a in m.A])
         vs.append(z[:, obs])
         signs.append([sampler.sign_after(ev, j) for j in snaps])
     v = np.array(vs)
@@ -49,4 +51,4 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
     mean, se, part = estimator.estimate(v, sg, gn)
     return {"v": v, "sign": sg, "gnorm": gn, "mean": mean, "stderr": se,
             "partials": part, "nu": np.array(nus), "stats": stats, "plan": plan,
-            "snaps": snaps}
+            "snaps": snaps, "states": states}

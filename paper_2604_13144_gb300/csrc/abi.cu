@@ -591,6 +591,58 @@ int tepai_dev_set_sample_offset(void* d_ws, long long sample_offset) {
   return TEPAI_OK;
 }
 
+int tepai_evolve_state(tepai_ctx* c, const tepai_problem* P, const tepai_params* Q, const tepai_mps* init,
+                       int* bond_dims, double* tensors, long long capacity, long long* used) {
+  if (!c || !P || !Q || !bond_dims || !tensors || !used || capacity < 0 || Q->n_samples != 1)
+    return TEPAI_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  HostPlan hp;
+  int rc = build_plan(P, Q, hp);
+  if (rc) return rc;
+  size_t ws_bytes = 0;
+  rc = tepai_dev_workspace_size(P, Q, 0, &ws_bytes);
+  if (rc) return rc;
+  const size_t mo = (size_t)hp.M * hp.n_obs;
+  const size_t cap = (size_t)Q->chi_max;
+  const size_t sdoubles = (size_t)hp.n * 2 * cap * cap * 2;
+  const size_t o_state = al256(sizeof(double) * 5 * mo);
+  const size_t o_dims = al256(o_state + sizeof(double) * sdoubles);
+  rc = ctx_reserve(c, ws_bytes, o_dims + sizeof(int) * (hp.n + 1) + 256);
+  if (rc) return rc;
+  rc = prepare_impl(P, Q, init, true, c->ws, c->ws_bytes, 0, c->stream);
+  if (rc) return rc;
+  char* ob = reinterpret_cast<char*>(c->out);
+  double* d_state = reinterpret_cast<double*>(ob + o_state);
+  int* d_dims = reinterpret_cast<int*>(ob + o_dims);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_reg.find(c->ws);
+    if (it == g_reg.end()) return TEPAI_ERR_INVALID_ARG;
+    it->second.ka.state_out = d_state;
+    it->second.ka.state_dims = d_dims;
+  }
+  rc = execute_impl(c->ws, c->out, nullptr, nullptr, nullptr, nullptr, c->stream);
+  if (rc) return rc;
+  std::vector<int> dims(hp.n + 1, 0);
+  CK(cudaMemcpyAsync(dims.data(), d_dims, sizeof(int) * (hp.n + 1), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  tepai_stats st{};
+  rc = stats_impl(c->ws, &st, c->stream);
+  if (rc) return rc;
+  if (st.device_status[0] != 0) return TEPAI_ERR_DEVICE_CHECK;
+  long long need = 0;
+  for (int i = 0; i < hp.n; ++i) {
+    if (dims[i] < 1 || dims[i] > (int)cap || dims[i + 1] < 1 || dims[i + 1] > (int)cap) return TEPAI_ERR_DEVICE_CHECK;
+    need += 4LL * dims[i] * dims[i + 1];
+  }
+  for (int i = 0; i <= hp.n; ++i) bond_dims[i] = dims[i];
+  *used = need;
+  if (need > capacity) return TEPAI_ERR_WORKSPACE_TOO_SMALL;
+  CK(cudaMemcpyAsync(tensors, d_state, sizeof(double) * need, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return TEPAI_OK;
+}
+
 int tepai_dev_release(void* d_ws) {
   if (!d_ws) return TEPAI_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);

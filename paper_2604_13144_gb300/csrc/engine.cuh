@@ -341,6 +341,7 @@ struct Engine {
   __device__ void init_product();
   __device__ void init_from_tensors();
   __device__ void init_from_canonical();
+  __device__ void export_state(double* out, int* dims);
   __device__ void normalise_centre();
   // single-site unitary u (2x2 row-major) on site i
   __device__ void apply_1site(int i, const C u[4]);

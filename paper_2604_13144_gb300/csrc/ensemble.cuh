@@ -75,6 +75,26 @@ __device__ __noinline__ void Engine<R>::init_from_canonical() {
   __syncthreads();
 }
 
+// Write the MPS (any gauge; normalised) to out in the start-state layout:
+// site tensors A_p[d_p][2][d_{p+1}] concatenated over chain positions, complex
+// interleaved in FP64; bond dimensions to dims[0..n].
+template <typename R>
+__device__ __noinline__ void Engine<R>::export_state(double* out, int* dims) {
+  for (int i = tid(); i <= a.n; i += nt()) dims[i] = sm.dims[i];
+  size_t off = 0;
+  for (int i = 0; i < a.n; ++i) {
+    const size_t cnt = (size_t)sm.dims[i] * 2 * sm.dims[i + 1];
+    const C* p = S(i);
+    for (size_t e = tid(); e < cnt; e += nt()) {
+      const C v = p[e];
+      out[2 * (off + e)] = (double)v.re;
+      out[2 * (off + e) + 1] = (double)v.im;
+    }
+    off += cnt;
+  }
+  __syncthreads();
+}
+
 // Rescale the centre tensor (and so the state) to unit norm.
 template <typename R>
 __device__ __noinline__ void Engine<R>::normalise_centre() {
@@ -384,6 +404,7 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
         ++mi;
       }
     }
+    if (a.state_out && si == 0 && !eng.failed()) eng.export_state(a.state_out, a.state_dims);
   }
   if (threadIdx.x == 0) {
     const LocalStats& st = eng.st;

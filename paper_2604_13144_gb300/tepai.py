@@ -21,7 +21,8 @@ TEPAI_FP64, TEPAI_MIXED = 0, 1
 EXPORTED = ["tepai_create", "tepai_destroy", "tepai_run", "tepai_sample_values",
             "tepai_export_circuit", "tepai_gnorm", "tepai_dev_workspace_size",
             "tepai_dev_prepare", "tepai_dev_execute", "tepai_dev_set_sample_offset",
-            "tepai_dev_stats", "tepai_dev_release", "tepai_autotune", "tepai_sample_values_static",
+            "tepai_dev_stats", "tepai_dev_release", "tepai_autotune", "tepai_evolve_state",
+            "tepai_sample_values_static",
             "tepai_strerror", "tepai_last_cuda_error"]
 
 
@@ -99,6 +100,7 @@ def _load():
         "tepai_dev_stats": (i, [vp, pS, vp]),
         "tepai_dev_release": (i, [vp]),
         "tepai_autotune": (i, [vp, pP, pQ, pM, ll, C.POINTER(i), pd]),
+        "tepai_evolve_state": (i, [vp, pP, pQ, pM, C.POINTER(i), pd, ll, C.POINTER(ll)]),
         "tepai_sample_values_static": (i, [pP, pQ, vp, vp, vp]),
         "tepai_strerror": (C.c_char_p, [i]),
         "tepai_last_cuda_error": (C.c_char_p, []),
@@ -210,6 +212,28 @@ def tepai_gnorm(prob, par):
     _check(_lib.tepai_gnorm(C.byref(m.prob), C.byref(m.par),
                             g.ctypes.data_as(C.POINTER(C.c_double)), C.byref(nu)), "tepai_gnorm")
     return g, nu.value
+
+
+def tepai_evolve_state(ctx, prob, par, init=None):
+    """Final MPS of one circuit (par.n_samples == 1) as (tensors, dims): tensors
+    in chain order, each (d_p, 2, d_{p+1}) complex128, in the layout `init`
+    takes (so the result can start later runs)."""
+    m = Marshalled(prob, par, init)
+    n, cap = int(prob.n), int(par.chi_max)
+    dims = np.zeros(n + 1, dtype=np.int32)
+    buf = np.zeros(n * 2 * cap * cap * 2)
+    used = C.c_longlong()
+    _check(_lib.tepai_evolve_state(ctx, C.byref(m.prob), C.byref(m.par), m.init_ptr(),
+                                   dims.ctypes.data_as(C.POINTER(C.c_int)),
+                                   buf.ctypes.data_as(C.POINTER(C.c_double)), buf.size, C.byref(used)),
+           "tepai_evolve_state")
+    flat = buf[:int(used.value)].view(np.complex128)
+    tensors, off = [], 0
+    for p in range(n):
+        cnt = int(dims[p]) * 2 * int(dims[p + 1])
+        tensors.append(flat[off:off + cnt].reshape(int(dims[p]), 2, int(dims[p + 1])).copy())
+        off += cnt
+    return tensors, dims
 
 
 def tepai_autotune(ctx, prob, par, init=None, trial_steps: int = 1):
