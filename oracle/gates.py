@@ -21,6 +21,16 @@ SWAP = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]],
                 dtype=np.complex128)
 
 
+# Single-site codes of initial product states and of observables (Pauli
+# strings given per site): states |0>, |1>, |+>, |->, |+i>, |-i>; operators
+# I, X, Y, Z.
+_R2 = 1.0 / np.sqrt(2.0)
+STATE_CODE = {0: np.array([1, 0], dtype=np.complex128), 1: np.array([0, 1], dtype=np.complex128),
+              2: np.array([_R2, _R2], dtype=np.complex128), 3: np.array([_R2, -_R2], dtype=np.complex128),
+              4: np.array([_R2, 1j * _R2], dtype=np.complex128), 5: np.array([_R2, -1j * _R2], dtype=np.complex128)}
+PAULI_CODE = {0: I2, 1: X, 2: Y, 3: Z}
+
+
 def pauli_string(name: str) -> np.ndarray:
     """'Z' -> Z (2x2); 'XX' -> X (x) X (4x4)."""
     m = PAULI[name[0]]

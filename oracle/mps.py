@@ -78,12 +78,13 @@ class MPS:
 
 
 def product_state(bits, periodic: bool = False) -> MPS:
-    """|b_0 b_1 ...> over ring sites, stored in chain order."""
+    """Product state of single-site codes (gates.STATE_CODE: |0>, |1>, |+>,
+    |->, |+i>, |-i>) over ring sites, stored in chain order."""
     order = chain_order(len(bits), periodic)
     ts = []
     for site in order:
         a = np.zeros((1, 2, 1), dtype=np.complex128)
-        a[0, int(bits[site]), 0] = 1.0
+        a[0, :, 0] = gates.STATE_CODE[int(bits[site])]
         ts.append(a)
     return MPS(ts, 0, periodic)
 
@@ -271,8 +272,29 @@ def expect_z(m: MPS) -> np.ndarray:
     return out[np.array(m.pos)]
 
 
+def expect_string(m: MPS, codes) -> float:
+    """<psi| (x)_i P_{codes[i]} |psi> / <psi|psi> for a Pauli string given per
+    ring site i (gates.PAULI_CODE), by one left-to-right transfer-matrix
+    contraction over the whole chain (no use of the canonical form):
+      E_{p+1}[c,d] = sum_{a,b,s,t} E_p[a,b] conj(A_p[a,s,c]) O_p[s,t] A_p[b,t,d],
+    with O_p the operator at chain position p (identity where none)."""
+    n = m.n
+    ops = [gates.I2] * n
+    for site, c in enumerate(codes):
+        ops[m.pos[site]] = gates.PAULI_CODE[int(c)]
+    E = np.ones((1, 1), dtype=np.complex128)
+    N = np.ones((1, 1), dtype=np.complex128)
+    for p in range(n):
+        A = m.A[p]
+        OA = np.einsum('st,btd->bsd', ops[p], A)
+        E = np.einsum('ab,asc,bsd->cd', E, A.conj(), OA)
+        N = np.einsum('ab,asc,bsd->cd', N, A.conj(), A)
+    return float((E[0, 0] / N[0, 0]).real)
+
+
 def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
-               floor_rel: float = 1e-14, gap_rel: float = 1e-4, regauge: bool = False) -> np.ndarray:
+               floor_rel: float = 1e-14, gap_rel: float = 1e-4, regauge: bool = False,
+               strings=None) -> np.ndarray:
     cache = GateCache(plan)
     out = []
     e = 0
@@ -282,5 +304,5 @@ def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
             apply_event(m, plan, cache, int(events[e, 1]), int(events[e, 2]),
                         chi_max, cutoff, floor_rel, gap_rel, regauge)
             e += 1
-        out.append(expect_z(m))
+        out.append(expect_z(m) if strings is None else np.array([expect_string(m, r) for r in strings]))
     return np.array(out)

@@ -25,7 +25,11 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
     plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, par.variant)
     S = par.steps_run()
     snaps = planner.snapshot_steps(S, par.n_snapshots)
-    obs = (np.arange(prob.n) if par.obs_sites is None
+    strings = getattr(par, "obs_strings", None)
+    if strings is not None:
+        strings = np.asarray(strings, dtype=np.int64).reshape(-1, prob.n)
+    obs = (np.arange(prob.n) if strings is None and par.obs_sites is None
+           else np.arange(len(strings)) if strings is not None
            else np.asarray(par.obs_sites, dtype=np.int64))
     idx = (range(par.sample_offset, par.sample_offset + par.n_samples)
            if samples is None else samples)
@@ -34,13 +38,13 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
         ev = sampler.sample_events(plan, par.seed, s, S)
         nus.append(len(ev))
         if use_statevector:
-            z = sv.run_events(prob.init_bits, plan, ev, snaps)
+            z = sv.run_events(prob.init_bits, plan, ev, snaps, strings)
             stats.append({})
         else:
             m = (mps_mod.product_state(prob.init_bits, prob.periodic) if init_tensors is None
                  else mps_mod.canonicalize(init_tensors, prob.periodic))
             z = mps_mod.run_events(m, plan, ev, snaps, par.chi_max, par.cutoff, floor_rel, gap_rel,
-                                   regauge)
+                                   regauge, strings)
             stats.append(m.stats)
             states.append([a.copy() for a in m.A])
         vs.append(z[:, obs])

@@ -14,10 +14,22 @@ from .sampler import EV_B, EV_C, EV_T
 
 
 def basis_state(bits) -> np.ndarray:
-    n = len(bits)
-    psi = np.zeros((2,) * n, dtype=np.complex128)
-    psi[tuple(int(b) for b in bits)] = 1.0
+    """Product state of single-site codes (gates.STATE_CODE): 0/1 are the
+    basis states, 2..5 are |+>, |->, |+i>, |-i>."""
+    psi = np.ones((), dtype=np.complex128)
+    for b in bits:
+        psi = np.multiply.outer(psi, gates.STATE_CODE[int(b)])
     return psi
+
+
+def expect_string(psi: np.ndarray, codes) -> float:
+    """<psi| (x)_i P_{codes[i]} |psi> / <psi|psi> for a Pauli string given per site
+    (gates.PAULI_CODE): the operators are applied to a copy of the state."""
+    phi = psi
+    for i, c in enumerate(codes):
+        if int(c):
+            phi = apply_1(phi, gates.PAULI_CODE[int(c)], i)
+    return float((np.vdot(psi, phi) / np.vdot(psi, psi)).real)
 
 
 def apply_1(psi: np.ndarray, u: np.ndarray, i: int) -> np.ndarray:
@@ -61,8 +73,9 @@ def apply_event(psi: np.ndarray, plan, k: int, v: int) -> np.ndarray:
     return apply_2(psi, g, t.a, t.b)
 
 
-def run_events(bits, plan, events, snap_steps) -> np.ndarray:
-    """<Z_i> after each snapshot step; events in gate order."""
+def run_events(bits, plan, events, snap_steps, strings=None) -> np.ndarray:
+    """<Z_i> (or, with `strings`, each Pauli string's expectation) after each
+    snapshot step; events in gate order."""
     psi = basis_state(bits)
     out = []
     e = 0
@@ -71,7 +84,7 @@ def run_events(bits, plan, events, snap_steps) -> np.ndarray:
         while e < ne and events[e, 0] <= js:
             psi = apply_event(psi, plan, int(events[e, 1]), int(events[e, 2]))
             e += 1
-        out.append(expect_z(psi))
+        out.append(expect_z(psi) if strings is None else np.array([expect_string(psi, r) for r in strings]))
     return np.array(out)
 
 

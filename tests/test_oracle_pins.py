@@ -353,3 +353,58 @@ def test_folded_ring_order_keeps_bonds_within_distance_two(n):
     for i in range(n):
         assert abs(pos[i] - pos[(i + 1) % n]) <= 2
     assert M.chain_order(n, False) == list(range(n))
+
+
+# ---- general observables and product initial states ----------------------
+
+def test_pauli_strings_mps_equal_state_vector():
+    """Two independent evaluations of Pauli-string expectations (full-chain MPS
+    contraction vs. operators applied to the dense state vector) agree on an
+    evolved, untruncated state; ring order included."""
+    from oracle import mps as M, statevector as S, planner as Pl, sampler as Sa
+    n = 6
+    prob = W.spin_ring(n, 1.0, seed=4)
+    prob.init_bits = np.array([2, 0, 5, 1, 3, 4], dtype=np.uint8)
+    plan = Pl.make_plan(prob, 0.3, 40, math.pi / 32, 0)
+    ev = Sa.sample_events(plan, 7, 3, 40)
+    m = M.product_state(prob.init_bits, True)
+    M.run_events(m, plan, ev, [40], 64, 0.0)
+    psi = S.basis_state(prob.init_bits)
+    for e in ev:
+        psi = S.apply_event(psi, plan, int(e[1]), int(e[2]))
+    rng = np.random.default_rng(1)
+    for _ in range(12):
+        codes = np.zeros(n, dtype=np.int64)
+        k = int(rng.integers(1, 4))
+        sites = rng.choice(n, size=k, replace=False)
+        codes[sites] = rng.integers(1, 4, size=k)
+        assert abs(M.expect_string(m, codes) - S.expect_string(psi, codes)) <= 1e-12
+
+
+def test_product_state_codes_give_single_site_values():
+    from oracle import mps as M
+    codes = np.array([0, 1, 2, 3, 4, 5], dtype=np.uint8)
+    m = M.product_state(codes, False)
+    want = {1: [0, 0, 1, -1, 0, 0], 2: [0, 0, 0, 0, 1, -1], 3: [1, -1, 0, 0, 0, 0]}
+    for p, vals in want.items():
+        for i, v in enumerate(vals):
+            s = np.zeros(6, dtype=np.int64)
+            s[i] = p
+            assert abs(M.expect_string(m, s) - v) <= 1e-15
+    # a string on a product state factorises: <X_2 Y_4 Z_0> = 1 * 1 * 1
+    assert abs(M.expect_string(m, np.array([3, 0, 1, 0, 2, 0])) - 1.0) <= 1e-15
+    assert abs(M.expect_string(m, np.array([3, 0, 1, 1, 0, 0])) + 1.0) <= 1e-15
+
+
+def test_two_site_heisenberg_from_plus_minus_gives_cos4t():
+    """H = XX + YY + ZZ on an open pair (no fields) from |+->: the three terms
+    commute, so the Trotter product is exact, and by SU(2) symmetry
+    <X_0>(t) = cos(4t), the X-basis image of the |01> case."""
+    prob = W.Problem(n=2, periodic=False, Jx=np.array([1.0]), Jy=np.array([1.0]), Jz=np.array([1.0]),
+                     h=np.zeros(2), init_bits=np.array([2, 3], dtype=np.uint8))
+    par = W.Params(T=0.7, n_steps=7, delta=0.5, n_samples=1, chi_max=4, cutoff=0.0, n_snapshots=7,
+                   seed=0, variant=2, obs_strings=np.array([[1, 0]]))
+    from oracle import run as oracle_run
+    r = oracle_run.run(prob, par)
+    ts = 0.1 * np.arange(1, 8)
+    assert np.allclose(r["v"][0, :, 0], np.cos(4 * ts), atol=1e-12, rtol=0)

@@ -50,9 +50,19 @@ class Params:
     precision: int = 0        # 0 FP64, 1 mixed (FP32 tensors, FP64 bookkeeping)
     run_steps: int = 0        # steps actually run (0 = all n_steps)
     obs_sites: np.ndarray | None = None   # Z_i sites; None = all sites
+    obs_strings: np.ndarray | None = None  # (n_obs, n) Pauli codes 0 I, 1 X, 2 Y, 3 Z per site;
+                                           # replaces obs_sites when given
 
     def steps_run(self) -> int:
         return self.n_steps if self.run_steps == 0 else self.run_steps
+
+
+def plus_minus_codes(n: int) -> np.ndarray:
+    """|+...+ - +...+>: |+> on every site except |-> on site n // 2 (single-site
+    state codes 2 and 3 of the product-state table)."""
+    c = np.full(n, 2, dtype=np.uint8)
+    c[n // 2] = 3
+    return c
 
 
 def neel_bits(n: int) -> np.ndarray:
