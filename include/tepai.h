@@ -66,7 +66,8 @@ typedef struct {
     int periodic;                  /* 1 = ring (bond n-1 joins sites n-1 and 0) */
     const double *Jx, *Jy, *Jz;    /* host, length n (ring) or n-1 (chain) */
     const double *h;               /* host, length n */
-    const unsigned char *init_bits;/* host, length n; initial |b_0 b_1 ...>, |0> has Z = +1 */
+    const unsigned char *init_bits;/* host, length n; initial product state, one code per site:
+                                      0 |0>, 1 |1> (Z|0> = |0>), 2 |+>, 3 |->, 4 |+i>, 5 |-i> */
 } tepai_problem;
 
 typedef struct {
@@ -89,6 +90,9 @@ typedef struct {
                                       2 = one 512-thread CTA per SM (shapes whose SVD working matrix
                                       is staged from global memory; otherwise ignored). The value
                                       tepai_autotune reports is the fastest on this device. */
+    const unsigned char *obs_strings; /* host, n_obs x n Pauli codes per site (0 I, 1 X, 2 Y, 3 Z):
+                                      observable o is the string (x)_i P_{o,i}; NULL = Z on
+                                      obs_sites. Values v[s][m][o] are <psi|P|psi>/<psi|psi>. */
 } tepai_params;
 
 /* Optional initial MPS shared by all samples (a "hybrid" start). Site tensors

@@ -60,7 +60,7 @@ int jacobi_precondition() {
 
 struct Layout {
   size_t terms, snaps, gnorm, obs, bits, dims, init, canon_meta, stats, counter, status, v, sign, arena, stride,
-      canon, total;
+      canon, ops, total;
 };
 
 Layout layout(const HostPlan& hp, const tepai_params* Q, int grid, bool has_init, size_t init_elems) {
@@ -73,6 +73,7 @@ Layout layout(const HostPlan& hp, const tepai_params* Q, int grid, bool has_init
   L.gnorm = o; o = al256(o + sizeof(double) * hp.M);
   L.obs = o; o = al256(o + sizeof(int) * hp.n_obs);
   L.bits = o; o = al256(o + hp.n);
+  L.ops = o; o = al256(o + hp.obs_ops.size());
   L.dims = o; o = al256(o + sizeof(int) * (hp.n + 1));
   L.init = o; o = al256(o + (has_init ? sizeof(double) * 2 * init_elems : 0));
   L.stats = o; o = al256(o + sizeof(DevStats));
@@ -191,6 +192,8 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   CK(cudaMemcpyAsync(base + L.gnorm, hp.gnorm.data(), sizeof(double) * hp.M, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + L.obs, hp.obs.data(), sizeof(int) * hp.n_obs, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + L.bits, hp.bits.data(), hp.n, cudaMemcpyHostToDevice, st));
+  if (!hp.obs_ops.empty())
+    CK(cudaMemcpyAsync(base + L.ops, hp.obs_ops.data(), hp.obs_ops.size(), cudaMemcpyHostToDevice, st));
   if (init) {
     CK(cudaMemcpyAsync(base + L.dims, init->bond_dims, sizeof(int) * (hp.n + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(base + L.init, init->tensors, sizeof(double) * 2 * init_elems,
@@ -209,6 +212,7 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   a.snaps = reinterpret_cast<const int*>(base + L.snaps);
   a.obs = reinterpret_cast<const int*>(base + L.obs);
   a.init_bits = reinterpret_cast<const unsigned char*>(base + L.bits);
+  a.obs_ops = hp.obs_ops.empty() ? nullptr : reinterpret_cast<const unsigned char*>(base + L.ops);
   a.init_dims = init ? reinterpret_cast<const int*>(base + L.dims) : nullptr;
   a.init_tensors = init ? reinterpret_cast<const double*>(base + L.init) : nullptr;
   a.arena = base + L.arena; a.arena_stride = L.stride;

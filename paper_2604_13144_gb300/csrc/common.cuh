@@ -91,6 +91,7 @@ struct KArgs {
   const int* init_dims;      // [n+1] or nullptr
   const char* canon;         // arena slot holding the start state in canonical form, or nullptr
   int* canon_meta;           // [n+2]: its bond dimensions, then its centre
+  const unsigned char* obs_ops;  // [n_obs][n] Pauli codes in chain order, or nullptr (Z on obs)
   double* state_out;         // final MPS of the call's first sample (FP64, dims-packed), or nullptr
   int* state_dims;           // [n+1] its bond dimensions
   const double* init_tensors;// complex interleaved FP64, or nullptr

@@ -376,6 +376,7 @@ struct Engine {
   __device__ void apply_event(int k, int v, int& sign_count);
   // measurement
   __device__ void measure_z(double* out_v);
+  __device__ void measure_strings(double* out_v);
 };
 
 }  // namespace tepai

@@ -10,11 +10,18 @@ namespace tepai {
 template <typename R>
 __device__ __noinline__ void Engine<R>::init_product() {
   for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = 1;
+  // single-site codes 0 |0>, 1 |1>, 2 |+>, 3 |->, 4 |+i>, 5 |-i>
+  const R r = (R)0.70710678118654752440;
   for (int i = tid(); i < a.n; i += nt()) {
     C* p = S(i);
-    const int b = a.init_bits[i] ? 1 : 0;
-    p[0] = C{b == 0 ? R(1) : R(0), 0};
-    p[1] = C{b == 1 ? R(1) : R(0), 0};
+    const int b = a.init_bits[i];
+    if (b <= 1) {
+      p[0] = C{b == 0 ? R(1) : R(0), 0};
+      p[1] = C{b == 1 ? R(1) : R(0), 0};
+    } else {
+      p[0] = C{r, 0};
+      p[1] = b == 2 ? C{r, 0} : b == 3 ? C{-r, 0} : b == 4 ? C{0, r} : C{0, -r};
+    }
   }
   centre = 0;
   __syncthreads();
@@ -330,6 +337,112 @@ __device__ __noinline__ void Engine<R>::measure_z(double* zout) {
   __syncthreads();
 }
 
+// <P_o> / <psi|psi> for Pauli-string observables (a.obs_ops: codes 0 I, 1 X,
+// 2 Y, 3 Z per chain position). With the centre on site c, sites left of c are
+// left-orthonormal and sites right of c right-orthonormal, so the contraction
+// only runs over chain positions lo = min(first, c) .. hi = max(last, c) of
+// the string's support: E = I at bond lo, then per site
+//   T^t[a][d] = sum_b E[a][b] A[b][t][d],  U^s = sum_t O[s][t] T^t,
+//   E'[c][d]  = sum_{a,s} conj(A[a][s][c]) U^s[a][d],
+// and <P> = Tr E at bond hi + 1, divided by |centre|^2.
+template <typename R>
+__device__ __noinline__ void Engine<R>::measure_strings(double* out) {
+  if (failed()) return;
+  PhaseTimer pt(st, PH_MEASURE);
+  const int n = a.n, c = centre;
+  C* E = TH;
+  C* Tm = TH + (size_t)cap * cap;
+  const bool use_gemm = a.smem_x_elems >= gemm_tile_elems(nt());
+  C* tile = reinterpret_cast<C*>(sm.x);
+  double nrm = 0.0;
+  {
+    const int cnt = sm.dims[c] * 2 * sm.dims[c + 1];
+    const C* p = S(c);
+    for (int e2 = tid(); e2 < cnt; e2 += nt()) nrm += (double)abs2(p[e2]);
+    nrm = block_sum(nrm, sm.red);
+  }
+  for (int o = 0; o < a.n_obs; ++o) {
+    const unsigned char* ops = a.obs_ops + (size_t)o * n;
+    int first = n, last = -1;
+    for (int p = 0; p < n; ++p)
+      if (ops[p]) { if (first == n) first = p; last = p; }
+    if (last < 0) {
+      if (tid() == 0) out[o] = 1.0;
+      continue;
+    }
+    const int lo = min(first, c), hi = max(last, c);
+    {
+      const int d = sm.dims[lo];
+      for (int e2 = tid(); e2 < d * d; e2 += nt()) E[e2] = C{(e2 / d == e2 % d) ? R(1) : R(0), 0};
+    }
+    __syncthreads();
+    for (int p = lo; p <= hi; ++p) {
+      const int dl = sm.dims[p], dr = sm.dims[p + 1];
+      const C* A = S(p);
+      if (use_gemm) {
+        block_gemm<R>(dl, 2 * dr, dl, tile,
+            [=](int ii, int kk) { return E[(size_t)ii * dl + kk]; },
+            [=](int kk, int jj) { return A[(size_t)kk * 2 * dr + jj]; },
+            [=](int ii, int jj, C v) {
+              const int s = jj >= dr, bb = jj - s * dr;
+              Tm[(size_t)s * dl * dr + (size_t)ii * dr + bb] = v;
+            });
+      } else {
+        for (int e2 = tid(); e2 < 2 * dl * dr; e2 += nt()) {
+          const int s = e2 / (dl * dr), rem = e2 - s * dl * dr, aa = rem / dr, bb = rem - aa * dr;
+          C acc = {0, 0};
+          for (int q = 0; q < dl; ++q) fma_c(acc, E[(size_t)aa * dl + q], A[(size_t)(q * 2 + s) * dr + bb]);
+          Tm[e2] = acc;
+        }
+      }
+      __syncthreads();
+      const int code = ops[p];
+      if (code) {
+        const size_t h = (size_t)dl * dr;
+        for (size_t e2 = tid(); e2 < h; e2 += nt()) {
+          const C t0 = Tm[e2], t1 = Tm[h + e2];
+          C u0, u1;
+          if (code == 1) { u0 = t1; u1 = t0; }                                      // X
+          else if (code == 2) { u0 = C{t1.im, -t1.re}; u1 = C{-t0.im, t0.re}; }    // Y: -i t1, i t0
+          else { u0 = t0; u1 = C{-t1.re, -t1.im}; }                                // Z
+          Tm[e2] = u0;
+          Tm[h + e2] = u1;
+        }
+        __syncthreads();
+      }
+      if (use_gemm) {
+        block_gemm<R>(dr, dr, 2 * dl, tile,
+            [=](int ii, int kk) {
+              const int s = kk >= dl, q = kk - s * dl;
+              const C u = A[(size_t)(q * 2 + s) * dr + ii];
+              return C{u.re, -u.im};
+            },
+            [=](int kk, int jj) { return Tm[(size_t)kk * dr + jj]; },
+            [=](int ii, int jj, C v) { E[(size_t)ii * dr + jj] = v; });
+        __syncthreads();
+      } else {
+        for (int e2 = tid(); e2 < dr * dr; e2 += nt()) {
+          const int b1 = e2 / dr, b2 = e2 - b1 * dr;
+          C acc = {0, 0};
+          for (int s = 0; s < 2; ++s)
+            for (int q = 0; q < dl; ++q)
+              fma_cc(acc, A[(size_t)(q * 2 + s) * dr + b1], Tm[(size_t)s * dl * dr + (size_t)q * dr + b2]);
+          XG[e2] = acc;
+        }
+        __syncthreads();
+        for (int e2 = tid(); e2 < dr * dr; e2 += nt()) E[e2] = XG[e2];
+        __syncthreads();
+      }
+    }
+    const int d = sm.dims[hi + 1];
+    double tr = 0.0;
+    for (int i = tid(); i < d; i += nt()) tr += (double)E[(size_t)i * d + i].re;
+    tr = block_sum(tr, sm.red);
+    if (tid() == 0) out[o] = tr / nrm;
+    __syncthreads();
+  }
+}
+
 // The TE-PAI sampler draw of gate (j, k) for global sample s: Philox4x64-10 with
 // key (seed, s) and counter (j, k, 0, 0); word 0 against floor(q_k 2^64) decides
 // "not A", word 1 against floor(r_k 2^64) decides C over B.
@@ -399,7 +512,8 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
       __syncthreads();
       if (eng.failed()) break;
       while (mi < a.M && a.snaps[mi] == j) {
-        eng.measure_z(a.v + ((size_t)si * a.M + mi) * a.n_obs);
+        if (a.obs_ops) eng.measure_strings(a.v + ((size_t)si * a.M + mi) * a.n_obs);
+        else eng.measure_z(a.v + ((size_t)si * a.M + mi) * a.n_obs);
         if (threadIdx.x == 0) a.sign[(size_t)si * a.M + mi] = (sign_count & 1) ? -1 : 1;
         ++mi;
       }

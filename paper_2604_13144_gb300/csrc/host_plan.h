@@ -23,6 +23,7 @@ struct FixedVec {
   void push_back(const T& v) { if (n < N) buf[n++] = v; else overflow = true; }
   const T* data() const { return buf; }
   size_t size() const { return n; }
+  bool empty() const { return n == 0; }
   const T& operator[](size_t i) const { return buf[i]; }
   T& operator[](size_t i) { return buf[i]; }
 };
@@ -36,13 +37,15 @@ struct PlanT {
   Vec<double> gnorm;
   Vec<int> obs;
   Vec<unsigned char> bits;
+  Vec<unsigned char> obs_ops;   // Pauli-string observables: [n_obs][n] codes in chain order
   double gnorm_step = 1.0, expected_nu = 0.0;
   void reset() {
     n = L = M = n_obs = periodic = 0; N = run_steps = 0; gnorm_step = 1.0; expected_nu = 0.0;
-    terms.clear(); snaps.clear(); gnorm.clear(); obs.clear(); bits.clear();
+    terms.clear(); snaps.clear(); gnorm.clear(); obs.clear(); bits.clear(); obs_ops.clear();
   }
   bool overflowed() const;
   void bits_set(int p, unsigned char v) { if ((size_t)p < bits.size()) bits[p] = v; }
+  void ops_set(size_t p, unsigned char v) { if (p < obs_ops.size()) obs_ops[p] = v; }
 };
 
 template <typename T> using HeapVec = std::vector<T>;
@@ -56,7 +59,8 @@ template <> struct FixedCap<double> { static constexpr size_t value = kFixedMaxM
 template <typename T> using FixedVecT = FixedVec<T, FixedCap<T>::value>;
 using FixedPlan = PlanT<FixedVecT>;
 template <> inline bool FixedPlan::overflowed() const {
-  return terms.overflow || snaps.overflow || gnorm.overflow || obs.overflow || bits.overflow;
+  return terms.overflow || snaps.overflow || gnorm.overflow || obs.overflow || bits.overflow ||
+         obs_ops.overflow;
 }
 
 inline bool finite_arr(const double* p, int n) {
@@ -135,7 +139,20 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   if (Q->n_snapshots < 1 || S % Q->n_snapshots != 0) return TEPAI_ERR_INVALID_ARG;
   hp.reset();
   hp.n = n; hp.periodic = P->periodic ? 1 : 0; hp.N = Q->n_steps; hp.run_steps = S; hp.M = Q->n_snapshots;
-  if (Q->obs_sites) {
+  if (Q->obs_strings) {
+    // observable o = Pauli string over physical sites, stored in chain order
+    if (Q->n_obs < 1) return TEPAI_ERR_INVALID_ARG;
+    for (int o = 0; o < Q->n_obs; ++o) {
+      hp.obs.push_back(0);
+      for (int p = 0; p < n; ++p) hp.obs_ops.push_back(0);
+    }
+    for (int o = 0; o < Q->n_obs; ++o)
+      for (int i = 0; i < n; ++i) {
+        const unsigned char code = Q->obs_strings[(size_t)o * n + i];
+        if (code > 3) return TEPAI_ERR_INVALID_ARG;
+        hp.ops_set((size_t)o * n + chain_pos(i, n, P->periodic), code);
+      }
+  } else if (Q->obs_sites) {
     if (Q->n_obs < 1) return TEPAI_ERR_INVALID_ARG;
     for (int o = 0; o < Q->n_obs; ++o) {
       if (Q->obs_sites[o] < 0 || Q->obs_sites[o] >= n) return TEPAI_ERR_INVALID_ARG;
@@ -147,7 +164,10 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   hp.n_obs = (int)hp.obs.size();
   // initial bits in chain order
   for (int p = 0; p < n; ++p) hp.bits.push_back(0);
-  for (int i = 0; i < n; ++i) hp.bits_set(chain_pos(i, n, P->periodic), P->init_bits[i] ? 1 : 0);
+  for (int i = 0; i < n; ++i) {
+    if (P->init_bits[i] > 5) return TEPAI_ERR_INVALID_ARG;
+    hp.bits_set(chain_pos(i, n, P->periodic), P->init_bits[i]);
+  }
   // term list: Z_0..Z_{n-1}, then per bond b: XX_b, YY_b, ZZ_b
   struct T0 { int kind, a, b, pauli; double c; };
   hp.L = n + 3 * nb;

@@ -75,6 +75,7 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
   const size_t o_snaps = o; o = a256(o + sizeof(int) * hp.M);
   const size_t o_obs = o; o = a256(o + sizeof(int) * hp.n_obs);
   const size_t o_bits = o; o = a256(o + hp.n);
+  const size_t o_ops = o; o = a256(o + hp.obs_ops.size());
   const size_t o_stats = o; o = a256(o + sizeof(DevStats));
   const size_t o_counter = o; o = a256(o + sizeof(unsigned long long));
   const size_t o_status = o; o = a256(o + 4 * sizeof(int));
@@ -105,6 +106,8 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
       cudaMemcpyAsync(base + o_snaps, hp.snaps.data(), sizeof(int) * hp.M, cudaMemcpyHostToDevice, st) ||
       cudaMemcpyAsync(base + o_obs, hp.obs.data(), sizeof(int) * hp.n_obs, cudaMemcpyHostToDevice, st) ||
       cudaMemcpyAsync(base + o_bits, hp.bits.data(), hp.n, cudaMemcpyHostToDevice, st) ||
+      (!hp.obs_ops.empty() &&
+       cudaMemcpyAsync(base + o_ops, hp.obs_ops.data(), hp.obs_ops.size(), cudaMemcpyHostToDevice, st)) ||
       cudaMemsetAsync(base + o_stats, 0, o_arena - o_stats, st))
     return TEPAI_ERR_CUDA;
   KArgs a{};
@@ -120,6 +123,7 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
   a.snaps = reinterpret_cast<const int*>(base + o_snaps);
   a.obs = reinterpret_cast<const int*>(base + o_obs);
   a.init_bits = reinterpret_cast<const unsigned char*>(base + o_bits);
+  a.obs_ops = hp.obs_ops.empty() ? nullptr : reinterpret_cast<const unsigned char*>(base + o_ops);
   a.arena = base + o_arena; a.arena_stride = stride;
   a.v = d_v; a.sign = d_sign;
   a.stats = reinterpret_cast<DevStats*>(base + o_stats);

@@ -47,7 +47,7 @@ class Params(C.Structure):
                 ("run_steps", C.c_longlong), ("chi_max", C.c_int), ("cutoff", C.c_double),
                 ("n_snapshots", C.c_int), ("obs_sites", C.POINTER(C.c_int)), ("n_obs", C.c_int),
                 ("seed", C.c_ulonglong), ("variant", C.c_int), ("precision", C.c_int),
-                ("launch_variant", C.c_int)]
+                ("launch_variant", C.c_int), ("obs_strings", C.POINTER(C.c_ubyte))]
 
 
 class Mps(C.Structure):
@@ -134,7 +134,13 @@ class Marshalled:
         self.prob = Problem(int(prob.n), int(bool(prob.periodic)), dp(self.Jx), dp(self.Jy),
                             dp(self.Jz), dp(self.h), self.bits.ctypes.data_as(C.POINTER(C.c_ubyte)))
         obs = getattr(par, "obs_sites", None)
-        if obs is not None:
+        strings = getattr(par, "obs_strings", None)
+        self.strings = None
+        if strings is not None:
+            self.strings = np.ascontiguousarray(np.asarray(strings).reshape(-1, int(prob.n)), dtype=np.uint8)
+            self.obs = None
+            obs_p, nobs = None, int(self.strings.shape[0])
+        elif obs is not None:
             self.obs = np.ascontiguousarray(obs, dtype=np.int32)
             obs_p, nobs = self.obs.ctypes.data_as(C.POINTER(C.c_int)), len(self.obs)
         else:
@@ -144,8 +150,10 @@ class Marshalled:
                           int(getattr(par, "sample_offset", 0)), int(getattr(par, "run_steps", 0)),
                           int(par.chi_max), float(par.cutoff), int(par.n_snapshots), obs_p, nobs,
                           int(par.seed) & (2**64 - 1), int(getattr(par, "variant", 0)),
-                          int(getattr(par, "precision", 0)), int(getattr(par, "launch_variant", 0)))
-        self.n_obs = nobs if obs is not None else int(prob.n)
+                          int(getattr(par, "precision", 0)), int(getattr(par, "launch_variant", 0)),
+                          self.strings.ctypes.data_as(C.POINTER(C.c_ubyte)) if self.strings is not None
+                          else None)
+        self.n_obs = nobs if (obs is not None or self.strings is not None) else int(prob.n)
         self.M = int(par.n_snapshots)
         self.init = None
         if init is not None:

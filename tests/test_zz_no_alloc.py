@@ -56,3 +56,25 @@ def test_static_scratch_rejects_sizes_beyond_its_limit(T):
     with pytest.raises(T.TepaiError) as e:
         T.tepai_sample_values_static(prob, par, v, sg)
     assert e.value.code == 6
+
+
+def test_static_scratch_with_pauli_string_observables(T):
+    import torch
+    n = 8
+    prob = W.spin_ring(n, 1.0, seed=1)
+    strings = np.zeros((3, n), dtype=np.uint8)
+    strings[0, 1] = 2
+    strings[1, [2, 3]] = [3, 3]
+    strings[2, [0, 4, 7]] = [1, 2, 3]
+    par = W.Params(T=0.3, n_steps=60, delta=math.pi / 64, n_samples=4, chi_max=16, cutoff=0.0,
+                   n_snapshots=3, seed=9, precision=0, obs_strings=strings)
+    ctx = T.tepai_create(0)
+    try:
+        ref = T.tepai_sample_values(ctx, prob, par)["v"]
+    finally:
+        T.tepai_destroy(ctx)
+    dv = torch.zeros((4, 3, 3), dtype=torch.float64, device="cuda")
+    ds = torch.zeros((4, 3), dtype=torch.int8, device="cuda")
+    T.tepai_sample_values_static(prob, par, dv, ds)
+    torch.cuda.synchronize()
+    assert float(np.max(np.abs(dv.cpu().numpy() - ref))) <= 1e-12
