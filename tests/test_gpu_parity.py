@@ -252,12 +252,12 @@ def test_results_independent_of_grid(T, ctx):
 
 # ------------------------------------------------------------------ full-size bench workload
 def test_bench_workload_sampled_parity(T):
-    """The launch bench.py times (chi = 128, n = 64, batch = 4 per SM, default launch
-    shape, shared random MPS at the cap): sampled samples of the batch against the
-    oracle, one by one."""
+    """The launch bench.py times (chi = 128, n = 64, 16 samples per SM, one Trotter
+    step, default launch shape, shared random MPS at the cap): sampled samples of
+    the batch against the oracle, one by one."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    batch = 4 * sms
+    batch = 16 * sms
     prob, par, init = W.bench_workload(batch, window_steps=1, sample_offset=777)
     run = T.DeviceRun(prob, par, init)
     v = torch.zeros((batch, 1, prob.n), dtype=torch.float64, device="cuda")
