@@ -86,10 +86,12 @@ typedef struct {
     unsigned long long seed;       /* Philox4x64-10 key word 0 (key word 1 = global sample index) */
     int variant;                   /* TEPAI_UNBIASED | TEPAI_NO_PI | TEPAI_TROTTER */
     int precision;                 /* TEPAI_FP64 | TEPAI_MIXED */
-    int launch_variant;            /* 0 = built-in launch-shape rule; 1 = two 256-thread CTAs per SM,
-                                      2 = one 512-thread CTA per SM (shapes whose SVD working matrix
-                                      is staged from global memory; otherwise ignored). The value
-                                      tepai_autotune reports is the fastest on this device. */
+    int launch_variant;            /* 0 = built-in launch-shape rule. When the SVD working matrix is
+                                      staged from global memory: 1 = two 256-thread CTAs per SM,
+                                      2 = one 512-thread CTA per SM. When it fits in shared memory:
+                                      3, 4, 5, 6 = 64, 128, 256, 512 threads per CTA (smaller CTAs
+                                      run more samples per SM). Variants that do not apply are
+                                      ignored. tepai_autotune reports the fastest on this device. */
     const unsigned char *obs_strings; /* host, n_obs x n Pauli codes per site (0 I, 1 X, 2 Y, 3 Z):
                                       observable o is the string (x)_i P_{o,i}; NULL = Z on
                                       obs_sites. Values v[s][m][o] are <psi|P|psi>/<psi|psi>. */

@@ -670,9 +670,9 @@ int tepai_autotune(tepai_ctx* c, const tepai_problem* P, const tepai_params* Q, 
   if (rc) return rc;
   int best = 0;
   double best_r = -1.0;
-  LaunchShape seen[3];
+  LaunchShape seen[7];
   int n_seen = 0;
-  for (int v = 1; v <= 2; ++v) {
+  for (int v = 1; v <= 6; ++v) {
     tepai_params q = *Q;
     q.launch_variant = v;
     q.n_snapshots = 1;

@@ -354,12 +354,13 @@ struct Engine {
   __device__ void panel_t(const C* V, int m, int j0, int bp, C* T);
   __device__ void apply_block_reflector(const C* V, int m, int j0, int bp, const C* T, bool herm,
                                         C* G, int c0, int c1, C* CH, C* CH1, C* Wm);
-  // QR of Y (global or shared): blocked when Y is in global memory and the
-  // staging buffer holds a panel and a chunk
+  // QR of Y (global or shared): blocked when Y is in global memory, the
+  // staging buffer holds a panel and a chunk, and the CTA has the 256 threads
+  // the 16 x 16 block-reflector steps use
   __device__ void qr_factor(C* Y, int m, int nq, C* Q, double tiny2) {
     const C* xs = reinterpret_cast<const C*>(sm.x);
     const bool y_in_smem = Y >= xs && Y < xs + a.smem_x_elems;
-    if (!y_in_smem && m >= 64 && (size_t)m * 32 + 512 <= (size_t)a.smem_x_elems)
+    if (!y_in_smem && m >= 64 && nt() >= 256 && (size_t)m * 32 + 512 <= (size_t)a.smem_x_elems)
       householder_blocked(Y, m, nq, Q, tiny2);
     else
       householder(Y, m, nq, Q, tiny2);

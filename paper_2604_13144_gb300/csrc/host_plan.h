@@ -132,7 +132,7 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   if (!(std::isfinite(Q->delta) && Q->delta > 0.0)) return TEPAI_ERR_INVALID_ARG;
   if (Q->chi_max < 1 || !(std::isfinite(Q->cutoff) && Q->cutoff >= 0.0)) return TEPAI_ERR_INVALID_ARG;
   if (Q->variant < 0 || Q->variant > 2 || Q->precision < 0 || Q->precision > 1) return TEPAI_ERR_INVALID_ARG;
-  if (Q->launch_variant < 0 || Q->launch_variant > 2) return TEPAI_ERR_INVALID_ARG;
+  if (Q->launch_variant < 0 || Q->launch_variant > 6) return TEPAI_ERR_INVALID_ARG;
   if (Q->n_samples < 0 || Q->sample_offset < 0) return TEPAI_ERR_INVALID_ARG;
   const long long S = Q->run_steps ? Q->run_steps : Q->n_steps;
   if (S < 1 || S > Q->n_steps) return TEPAI_ERR_INVALID_ARG;
@@ -246,8 +246,11 @@ struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems, per_s
 // latency and copy-wait stalls, and the modest staging leaves L1 room for
 // the global operands. If two do not fit, one 512-thread CTA per SM stages
 // blocks within 128 KB.
-// `variant` forces one staged shape: 1 = two 256-thread CTAs per SM, 2 = one
-// 512-thread CTA per SM; 0 (or a shape that does not apply) keeps the rule.
+// `variant` forces a shape. For a staged working matrix: 1 = two 256-thread
+// CTAs per SM, 2 = one 512-thread CTA per SM. For a working matrix held in
+// shared memory: 3, 4, 5, 6 = 64, 128, 256, 512 threads per CTA, so that small
+// bond dimensions run several samples per SM. 0 (or a variant that does not
+// apply) keeps the rule.
 template <class Occ>
 inline cudaError_t choose_launch_shape(int n, int L, int cap, int csize, int optin, Occ occ, LaunchShape& ls,
                                        int variant = 0) {
@@ -256,7 +259,7 @@ inline cudaError_t choose_launch_shape(int n, int L, int cap, int csize, int opt
   int per_sm = 1;
   cudaError_t e;
   if (fixed + xbytes <= (size_t)optin) {
-    ls.block = cap >= 64 ? 512 : 256;
+    ls.block = variant >= 3 && variant <= 6 ? (64 << (variant - 3)) : (cap >= 64 ? 512 : 256);
     ls.x_in_smem = 1;
     ls.x_elems = 4 * cap * cap;
     ls.smem = fixed + xbytes;

@@ -61,7 +61,7 @@ def test_invalid_arguments_are_rejected(T):
     with pytest.raises(T.TepaiError):
         T.tepai_gnorm(p2, par)
     bad = W.Params(**par.__dict__)
-    bad.launch_variant = 3                                  # variants are 0, 1, 2
+    bad.launch_variant = 7                                  # variants are 0 .. 6
     with pytest.raises(T.TepaiError) as e:
         T.tepai_gnorm(prob, bad)
     assert e.value.code == 1

@@ -84,3 +84,24 @@ def test_autotune_picks_a_variant_that_agrees_with_the_default(T):
             assert float(np.max(np.abs(got - ref))) <= TOL64, variant
     finally:
         T.tepai_destroy(ctx)
+
+
+def test_small_chi_variants_agree(T):
+    """Bond dimension 16 in FP64: the working matrix stays in shared memory, and
+    CTAs of 64, 128, 256 and 512 threads (several samples per SM for the small
+    ones) compute the same circuits."""
+    prob = W.spin_ring(8, 1.0, seed=0)
+    par = W.Params(T=0.4, n_steps=100, delta=math.pi / 64, n_samples=6, chi_max=16, cutoff=1e-12,
+                   n_snapshots=2, seed=3, precision=0)
+    ctx = T.tepai_create(0)
+    try:
+        ref = T.tepai_sample_values(ctx, prob, par)["v"]
+        for variant in (3, 4, 5, 6):
+            q = W.Params(**par.__dict__)
+            q.launch_variant = variant
+            got = T.tepai_sample_values(ctx, prob, q)["v"]
+            assert float(np.max(np.abs(got - ref))) <= TOL64, variant
+        best, rate = T.tepai_autotune(ctx, prob, par, None, trial_steps=20)
+        assert best in (1, 3, 4, 6) and rate > 0.0
+    finally:
+        T.tepai_destroy(ctx)
