@@ -15,7 +15,7 @@ import math
 
 import numpy as np
 
-UNBIASED, NO_PI, TROTTER = 0, 1, 2
+UNBIASED, NO_PI, TROTTER, CONTINUOUS = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
@@ -74,6 +74,9 @@ class Plan:
     variant: int
     n_steps: int
     delta: float
+    lam: np.ndarray = None     # CONTINUOUS: event rate of term k per unit time
+    r_inf: float = 0.0         # CONTINUOUS: probability that an event is C
+    T: float = 0.0             # total time of the product formula
 
 
 def make_plan(prob, T: float, n_steps: int, delta: float, variant: int = UNBIASED) -> Plan:
@@ -85,6 +88,22 @@ def make_plan(prob, T: float, n_steps: int, delta: float, variant: int = UNBIASE
     r = np.zeros(L)
     gn = np.zeros(L)
     phi = np.zeros(L)
+    lam = np.zeros(L)
+    r_inf = 0.0
+    if variant == CONTINUOUS:
+        # N -> infinity limit of the PAI draws (App. A.3 Eq. gammas at small
+        # theta): per unit time, term k leaves A with rate
+        # |c_k| (3 - cos Delta) / sin Delta (whose sum times T is nu_inf of
+        # App. A.5), and a non-A event is C with probability
+        # |gamma_3| / (|gamma_2| + |gamma_3|) -> (1 - cos Delta) / (3 - cos Delta).
+        rate = (3.0 - math.cos(delta)) / math.sin(delta)
+        r_inf = (1.0 - math.cos(delta)) / (3.0 - math.cos(delta))
+        for k, t in enumerate(terms):
+            lam[k] = abs(t.c) * rate
+            phi[k] = math.copysign(delta, t.c) if t.c != 0.0 else delta
+        return Plan(terms=terms, theta=theta, gam=gam, gnorm_gate=np.ones(L), q=q, r=np.full(L, r_inf),
+                    thr_event=[0] * L, thr_c=[threshold_u64(r_inf)] * L, phi=phi, gnorm_step=1.0,
+                    variant=variant, n_steps=n_steps, delta=delta, lam=lam, r_inf=r_inf, T=T)
     for k, th in enumerate(theta):
         if variant == TROTTER:
             # deterministic product formula: every gate is R_k(theta_k)
@@ -93,8 +112,8 @@ def make_plan(prob, T: float, n_steps: int, delta: float, variant: int = UNBIASE
             continue
         if variant == NO_PI:
             # App. A.4: gamma~_1 = 1 - lambda, gamma~_2 = lambda, lambda = |theta|/Delta
-            lam = abs(th) / delta
-            gam[k] = (1.0 - lam, lam, 0.0)
+            frac = abs(th) / delta
+            gam[k] = (1.0 - frac, frac, 0.0)
         else:
             gam[k] = gammas(th, delta)
         a = np.abs(gam[k])
@@ -111,12 +130,12 @@ def make_plan(prob, T: float, n_steps: int, delta: float, variant: int = UNBIASE
                 thr_event=[threshold_u64(x) for x in q],
                 thr_c=[threshold_u64(x) for x in r],
                 phi=phi, gnorm_step=gstep, variant=variant,
-                n_steps=n_steps, delta=delta)
+                n_steps=n_steps, delta=delta, lam=lam, r_inf=r_inf, T=T)
 
 
 def check_theta(plan: Plan) -> bool:
     """The PAI decomposition assumes |theta_kj| <= Delta <= pi (App. A.3)."""
-    if plan.variant == TROTTER:
+    if plan.variant in (TROTTER, CONTINUOUS):
         return True
     return bool(np.all(np.abs(plan.theta) <= plan.delta) and plan.delta <= math.pi)
 
@@ -124,6 +143,19 @@ def check_theta(plan: Plan) -> bool:
 def snapshot_steps(run_steps: int, M: int) -> list[int]:
     """Snapshot m = 1..M is taken after step j_m = m * run_steps / M."""
     return [m * run_steps // M for m in range(1, M + 1)]
+
+
+def snapshot_times(plan: Plan, run_steps: int, M: int) -> np.ndarray:
+    """CONTINUOUS: snapshot m = 1..M at time t_m = (T run_steps / N) m / M,
+    evaluated as t_run * m / M."""
+    t_run = plan.T * run_steps / plan.n_steps
+    return np.array([t_run * m / M for m in range(1, M + 1)])
+
+
+def gnorm_time(plan: Plan, t: float) -> float:
+    """CONTINUOUS: ||g(t)||_1 = exp[2 tan(Delta/2) ||c||_1 t] (Eq. overhead)."""
+    c1 = sum(abs(tm.c) for tm in plan.terms)
+    return math.exp(2.0 * math.tan(plan.delta / 2) * c1 * t)
 
 
 def gnorm_at(plan: Plan, j: int) -> float:

@@ -24,7 +24,13 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
     sample's final MPS (site tensors in chain order; MPS runs only)."""
     plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, par.variant)
     S = par.steps_run()
-    snaps = planner.snapshot_steps(S, par.n_snapshots)
+    cont = par.variant == planner.CONTINUOUS
+    if cont:
+        # snapshots are times; event rows carry their snapshot index m = 1..M
+        t_snaps = planner.snapshot_times(plan, S, par.n_snapshots)
+        snaps = list(range(1, par.n_snapshots + 1))
+    else:
+        snaps = planner.snapshot_steps(S, par.n_snapshots)
     strings = getattr(par, "obs_strings", None)
     if strings is not None:
         strings = np.asarray(strings, dtype=np.int64).reshape(-1, prob.n)
@@ -35,7 +41,8 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
            if samples is None else samples)
     vs, signs, nus, stats, states = [], [], [], [], []
     for s in idx:
-        ev = sampler.sample_events(plan, par.seed, s, S)
+        ev = (sampler.sample_events_continuous(plan, par.seed, s, t_snaps)[0] if cont
+              else sampler.sample_events(plan, par.seed, s, S))
         nus.append(len(ev))
         if use_statevector:
             z = sv.run_events(prob.init_bits, plan, ev, snaps, strings)
@@ -51,8 +58,10 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
         signs.append([sampler.sign_after(ev, j) for j in snaps])
     v = np.array(vs)
     sg = np.array(signs, dtype=np.int8)
-    gn = np.array([planner.gnorm_at(plan, j) for j in snaps])
+    gn = (np.array([planner.gnorm_time(plan, t) for t in t_snaps]) if cont
+          else np.array([planner.gnorm_at(plan, j) for j in snaps]))
     mean, se, part = estimator.estimate(v, sg, gn)
     return {"v": v, "sign": sg, "gnorm": gn, "mean": mean, "stderr": se,
             "partials": part, "nu": np.array(nus), "stats": stats, "plan": plan,
-            "snaps": snaps, "states": states}
+            "snaps": snaps, "states": states,
+            "times": (t_snaps if cont else np.array([par.T * j / par.n_steps for j in snaps]))}

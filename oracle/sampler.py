@@ -18,6 +18,8 @@ Events are returned in gate order (j ascending, then k ascending) as
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 from . import planner
@@ -45,6 +47,64 @@ def sample_events(plan: planner.Plan, seed: int, s: int, run_steps: int) -> np.n
     v = np.where(isc[sel], EV_C, EV_B)
     return np.stack([j[sel].astype(np.int64), k[sel].astype(np.int64),
                      v.astype(np.int64)], axis=1)
+
+
+def sample_events_continuous(plan: planner.Plan, seed: int, s: int, t_snaps) -> tuple:
+    """N -> infinity sampler (variant CONTINUOUS): term k emits events as a
+    Poisson process of rate lam_k on [0, t_snaps[-1]]. Event i (0-based) of term
+    k uses one Philox4x64-10 block with key (seed, s) and counter (k, i, 1, 0):
+    u = ((x0 >> 11) + 1) 2^-53 in (0, 1] gives the gap -ln(u) / lam_k since the
+    previous event (or t = 0), and x1 < floor(r_inf 2^64) makes it C. Events
+    are returned in time order as (m, k, v): m is the first snapshot with
+    t <= t_m, so (m, k, v) rows work with sign_after and the snapshot loops;
+    the times are returned alongside."""
+    t_end = float(t_snaps[-1])
+    L = len(plan.terms)
+    lam = np.asarray(plan.lam, dtype=np.float64)
+    live = [k for k in range(L) if lam[k] > 0.0]
+    rows, times = [], []
+    if not live:
+        return np.zeros((0, 3), dtype=np.int64), np.zeros(0)
+    # draw events i = 0 .. C-1 of every live term at once; a term whose C
+    # events all fall before t_end draws the next C (rare: C is the mean
+    # count plus eight standard deviations)
+    mu = float(np.max(lam)) * t_end
+    C = int(mu + 8.0 * math.sqrt(mu) + 16)
+
+    def draw(ks, i0):
+        kk = np.repeat(np.array(ks, dtype=np.uint64), C)
+        ii = np.tile(np.arange(i0, i0 + C, dtype=np.uint64), len(ks))
+        x0, x1, _, _ = philox4x64_vec(kk, ii, np.ones_like(kk), np.zeros_like(kk), seed, s)
+        return x0.reshape(len(ks), C), x1.reshape(len(ks), C)
+
+    X0, X1 = draw(live, 0)
+    for row, k in enumerate(live):
+        t, i0 = 0.0, 0
+        x0, x1 = X0[row], X1[row]
+        while True:
+            u = ((x0 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+            gap = -np.log(u) / lam[k]
+            tk = np.empty(C)
+            for e in range(C):          # t accumulates one gap at a time
+                t = t + gap[e]
+                tk[e] = t
+            n_ok = int(np.count_nonzero(tk <= t_end))
+            times.extend(tk[:n_ok].tolist())
+            isc = x1[:n_ok] < np.uint64(plan.thr_c[k])
+            rows.extend((k, EV_C if c else EV_B) for c in isc)
+            if n_ok < C:
+                break
+            i0 += C
+            x0, x1 = (a[0] for a in draw([k], i0))
+    order = sorted(range(len(times)), key=lambda e: (times[e], rows[e][0]))
+    ts = np.array([times[e] for e in order])
+    ev = np.zeros((len(order), 3), dtype=np.int64)
+    for r, e in enumerate(order):
+        m = 1
+        while ts[r] > t_snaps[m - 1]:
+            m += 1
+        ev[r] = (m, rows[e][0], rows[e][1])
+    return ev, ts
 
 
 def sign_after(events: np.ndarray, j: int) -> int:

@@ -408,3 +408,81 @@ def test_two_site_heisenberg_from_plus_minus_gives_cos4t():
     r = oracle_run.run(prob, par)
     ts = 0.1 * np.arange(1, 8)
     assert np.allclose(r["v"][0, :, 0], np.cos(4 * ts), atol=1e-12, rtol=0)
+
+
+# ---------------------------------------------------------------- P15
+def test_continuous_rates_are_the_finite_n_limit():
+    """The N -> infinity sampler's rates are the limits of the finite-N draw
+    probabilities built from Eq. gammas: q_k N / T -> lam_k, r_k -> r_inf,
+    ||g||_1 -> exp(2 tan(Delta/2) ||c||_1 T)."""
+    prob, par, _ = W.config(1)
+    cp = planner.make_plan(prob, par.T, par.n_steps, par.delta, planner.CONTINUOUS)
+    errs = []
+    for N in (10 ** 4, 10 ** 5, 10 ** 6):
+        fp = planner.make_plan(prob, par.T, N, par.delta)
+        e_lam = np.max(np.abs(fp.q * N / par.T - cp.lam) / cp.lam)
+        e_r = np.max(np.abs(fp.r - cp.r_inf)) / cp.r_inf
+        e_g = abs(fp.gnorm_step ** N / planner.gnorm_time(cp, par.T) - 1)
+        errs.append(max(e_lam, e_r, e_g))
+        assert np.array_equal(cp.phi, fp.phi)          # setting B = R_k(sign(theta) Delta)
+    # first-order convergence: the error falls tenfold per tenfold N
+    assert 8 < errs[0] / errs[1] < 12 and 8 < errs[1] / errs[2] < 12 and errs[2] < 5e-4
+    assert abs(np.sum(cp.lam) * par.T / planner.nu_infinity(prob, par.T, par.delta) - 1) < 1e-14
+
+
+def test_continuous_sampler_counts_and_times():
+    """Poisson law of the continuous sampler: per term, E[count] = lam_k t_M with
+    variance equal to the mean; the C fraction is r_inf; given the count, the
+    event times are uniform on [0, t_M] (mean t_M / 2)."""
+    prob = W.spin_ring(4, 1.0, seed=2)
+    par = W.Params(T=1.0, n_steps=100, delta=math.pi / 8, n_samples=1, chi_max=4, cutoff=0.0,
+                   n_snapshots=4, variant=planner.CONTINUOUS)
+    plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, planner.CONTINUOUS)
+    ts = planner.snapshot_times(plan, par.steps_run(), par.n_snapshots)
+    L = len(plan.terms)
+    Ns = 1500
+    cnt = np.zeros((Ns, L))
+    nc, tsum, ntot = 0, 0.0, 0
+    for s in range(Ns):
+        ev, tt = sampler.sample_events_continuous(plan, 11, s, ts)
+        assert np.all(np.diff(tt) >= 0) and np.all((tt > 0) & (tt <= ts[-1]))
+        # snapshot index: first m with t <= t_m
+        assert np.all(tt <= ts[ev[:, 0] - 1])
+        assert np.all((ev[:, 0] == 1) | (tt > ts[np.maximum(ev[:, 0] - 2, 0)]))
+        np.add.at(cnt[s], ev[:, 1], 1)
+        nc += int(np.sum(ev[:, 2] == sampler.EV_C))
+        tsum += float(np.sum(tt))
+        ntot += len(tt)
+    mu = plan.lam * ts[-1]
+    assert np.all(np.abs(cnt.mean(axis=0) - mu) < 4 * np.sqrt(mu / Ns))
+    tot = cnt.sum(axis=1)
+    assert abs(tot.var(ddof=1) / mu.sum() - 1) < 0.15
+    assert abs(nc / ntot - plan.r_inf) < 4 * math.sqrt(plan.r_inf * (1 - plan.r_inf) / ntot)
+    assert abs(tsum / ntot - ts[-1] / 2) < 4 * ts[-1] / math.sqrt(12 * ntot)
+
+
+def test_continuous_mean_is_unbiased_for_exact_evolution():
+    """In the N -> infinity limit the sampled circuits carry no Trotter error:
+    the signed, ||g||_1-weighted mean estimates <Z_i>(t) of exp(-iHt) itself."""
+    prob = W.spin_ring(4, 1.0, seed=3)
+    # |0>|+i>|1>|+>: a start state that is not real, so that <Z_i>(t) differs
+    # from <Z_i>(-t) and a sign error in the B rotations shows
+    prob.init_bits = np.array([0, 4, 1, 2])
+    par = W.Params(T=0.25, n_steps=100, delta=math.pi / 8, n_samples=3000, chi_max=4,
+                   cutoff=0.0, n_snapshots=4, seed=9, variant=planner.CONTINUOUS)
+    r = R.run(prob, par, use_statevector=True)
+    ze = sv.exact_z(prob, list(r["times"]))
+    assert np.all(np.abs(r["mean"] - ze) <= 4 * r["stderr"] + 1e-12)
+    # the estimate resolves the dynamics: exact values move well beyond the band
+    assert np.max(np.abs(ze - ze[0])) > 10 * np.max(r["stderr"])
+    assert abs(r["gnorm"][-1] - planner.gnorm_infinity(prob, par.T, par.delta)) < 1e-12
+
+
+def test_continuous_mps_equals_statevector():
+    prob = W.spin_ring(6, 1.0, seed=4)
+    par = W.Params(T=0.6, n_steps=100, delta=math.pi / 16, n_samples=3, chi_max=8,
+                   cutoff=0.0, n_snapshots=3, seed=2, variant=planner.CONTINUOUS)
+    r1 = R.run(prob, par)
+    r2 = R.run(prob, par, use_statevector=True)
+    assert np.max(np.abs(r1["v"] - r2["v"])) < 1e-12
+    assert np.array_equal(r1["sign"], r2["sign"]) and np.all(r1["nu"] > 0)

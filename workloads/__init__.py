@@ -46,7 +46,7 @@ class Params:
     n_snapshots: int          # M, snapshots at j_m = m * run_steps / M
     seed: int = 0             # circuit-sampler seed
     sample_offset: int = 0    # global index of the first sample
-    variant: int = 0          # 0 unbiased TE-PAI, 1 no-pi TE-PAI, 2 Trotter
+    variant: int = 0          # 0 unbiased TE-PAI, 1 no-pi TE-PAI, 2 Trotter, 3 N -> infinity TE-PAI
     precision: int = 0        # 0 FP64, 1 mixed (FP32 tensors, FP64 bookkeeping)
     run_steps: int = 0        # steps actually run (0 = all n_steps)
     obs_sites: np.ndarray | None = None   # Z_i sites; None = all sites
