@@ -54,6 +54,17 @@ extern "C" {
 #define TEPAI_UNBIASED 0  /* TE-PAI with settings A, B, C (App. A.3) */
 #define TEPAI_NO_PI    1  /* biased TE-PAI without pi-rotations (Statement 3; App. A.4) */
 #define TEPAI_TROTTER  2  /* deterministic first-order product formula (Eq. Trotter-Suzuki) */
+#define TEPAI_CONTINUOUS 3 /* TE-PAI in the limit N -> infinity (App. A.3 at small theta, App. A.5,
+                              Eq. overhead): term k fires B/C events as a Poisson process of rate
+                              |c_k| (3 - cos Delta) / sin Delta; an event is C with probability
+                              (1 - cos Delta) / (3 - cos Delta); ||g(t)||_1 =
+                              exp(2 tan(Delta/2) ||c||_1 t). Needs 0 < Delta < pi. The evolved
+                              time is T run_steps / n_steps; snapshot m is taken at that time
+                              times m / n_snapshots, after every event at or before it. Event i
+                              (from 0) of term k draws Philox4x64-10 counter (k, i, 1, 0) under
+                              key (seed, sample): u = ((x0 >> 11) + 1) 2^-53 gives the waiting
+                              time -ln(u) / rate, x1 < floor(P(C) 2^64) makes it C. Ties in time
+                              go to the lower term index. */
 
 #define TEPAI_FP64  0     /* all tensor arithmetic in FP64 */
 #define TEPAI_MIXED 1     /* FP32 tensors and SVD; FP64 norms, truncation weights and reduction */
@@ -84,7 +95,7 @@ typedef struct {
     const int *obs_sites;          /* host, Z_i sites measured; NULL = all n */
     int n_obs;
     unsigned long long seed;       /* Philox4x64-10 key word 0 (key word 1 = global sample index) */
-    int variant;                   /* TEPAI_UNBIASED | TEPAI_NO_PI | TEPAI_TROTTER */
+    int variant;                   /* TEPAI_UNBIASED | TEPAI_NO_PI | TEPAI_TROTTER | TEPAI_CONTINUOUS */
     int precision;                 /* TEPAI_FP64 | TEPAI_MIXED */
     int launch_variant;            /* 0 = built-in launch-shape rule. When the SVD working matrix is
                                       staged from global memory: 1 = two 256-thread CTAs per SM,
@@ -166,12 +177,17 @@ int tepai_sample_values(tepai_ctx *ctx, const tepai_problem *prob, const tepai_p
                         const tepai_mps *init, double *v, signed char *sign, tepai_stats *stats);
 
 /* The events of global sample `sample`, drawn by the device sampler, in gate
- * order. Writes min(count, cap) events to buf and the full count to *count. */
+ * order (j = step, from 1). For TEPAI_CONTINUOUS they come in time order and j
+ * is the snapshot index m (from 1) of the first t_m at or after the event.
+ * Writes min(count, cap) events to buf and the full count to *count. */
 int tepai_export_circuit(tepai_ctx *ctx, const tepai_problem *prob, const tepai_params *par,
                          long long sample, tepai_event *buf, long long cap, long long *count);
 
 /* Host planner only: g[m] = ||g(t_m)||_1 (App. A.6, finite-N product) and the
- * expected gate count per sample E[nu] = run_steps * sum_k q_k. */
+ * expected gate count per sample E[nu] = run_steps * sum_k q_k. For
+ * TEPAI_CONTINUOUS: g[m] = exp(2 tan(Delta/2) ||c||_1 t_m) and
+ * E[nu] = t_run sum_k rate_k (nu_inf of App. A.5 when run_steps = N); such
+ * a problem is refused with TEPAI_ERR_INVALID_ARG when E[nu] > 1e7. */
 int tepai_gnorm(const tepai_problem *prob, const tepai_params *par, double *g, double *expected_nu);
 
 /* ---- device-resident entry points -------------------------------------- */

@@ -153,7 +153,7 @@ int launch_shape(const HostPlan& hp, const tepai_params* Q, int grid_req, Launch
     return Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(block, smem, per_sm)
                                       : occupancy_ensemble_f32(block, smem, per_sm);
   };
-  CK(choose_launch_shape(hp.n, hp.L, Q->chi_max, nc.csize, optin, occ, ls, Q->launch_variant));
+  CK(choose_launch_shape(hp.n, hp.L, Q->variant == TEPAI_CONTINUOUS ? hp.L : 0, Q->chi_max, nc.csize, optin, occ, ls, Q->launch_variant));
   ls.grid = grid_req > 0 ? grid_req : sms * ls.per_sm;
   if (Q->n_samples > 0 && ls.grid > Q->n_samples) ls.grid = (int)Q->n_samples;
   if (ls.grid < 1) ls.grid = 1;
@@ -207,7 +207,7 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   a.n = hp.n; a.L = hp.L; a.M = hp.M; a.n_obs = hp.n_obs; a.chi_cap = Q->chi_max;
   a.periodic = hp.periodic; a.variant = Q->variant; a.max_sweeps = nc.max_sweeps;
   a.N = hp.N; a.run_steps = hp.run_steps; a.n_samples = Q->n_samples; a.sample_offset = Q->sample_offset;
-  a.seed = Q->seed; a.cutoff = Q->cutoff; a.floor_rel = nc.floor_rel; a.tol = nc.tol; a.gap_rel = nc.gap_rel;
+  a.seed = Q->seed; a.t_run = hp.t_run; a.cutoff = Q->cutoff; a.floor_rel = nc.floor_rel; a.tol = nc.tol; a.gap_rel = nc.gap_rel;
   a.terms = reinterpret_cast<const TermDev*>(base + L.terms);
   a.snaps = reinterpret_cast<const int*>(base + L.snaps);
   a.obs = reinterpret_cast<const int*>(base + L.obs);
@@ -535,7 +535,8 @@ int tepai_export_circuit(tepai_ctx* c, const tepai_problem* P, const tepai_param
   char* base = static_cast<char*>(c->ws);
   CK(cudaMemcpyAsync(base, hp.terms.data(), sizeof(TermDev) * hp.L, cudaMemcpyHostToDevice, c->stream));
   KArgs a{};
-  a.n = hp.n; a.L = hp.L; a.variant = Q->variant; a.run_steps = hp.run_steps; a.seed = Q->seed;
+  a.n = hp.n; a.L = hp.L; a.M = hp.M; a.variant = Q->variant; a.run_steps = hp.run_steps; a.seed = Q->seed;
+  a.t_run = hp.t_run;
   a.terms = reinterpret_cast<const TermDev*>(base);
   unsigned long long* d_count = reinterpret_cast<unsigned long long*>(base + tb);
   int* d_buf = reinterpret_cast<int*>(base + tb + 256);

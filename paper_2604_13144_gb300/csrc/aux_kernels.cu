@@ -48,8 +48,34 @@ cudaError_t launch_signed_reduce(const double* v, const signed char* sign, long 
 // ensemble kernel. One CTA; thread 0 appends in k order after each step.
 __global__ void export_circuit_kernel(const __grid_constant__ KArgs a, unsigned long long s, int* buf,
                                       long long cap, unsigned long long* count) {
-  extern __shared__ unsigned char flags[];
+  extern __shared__ __align__(16) unsigned char flags[];
   unsigned long long cnt = 0;
+  if (a.variant == 3) {
+    // N -> infinity sampler: thread 0 merges the terms' events in time order;
+    // an event's j is its snapshot index m (first m with t <= t_m)
+    double* tn = reinterpret_cast<double*>(flags + ((a.L + 15) / 16) * 16);
+    unsigned* ic = reinterpret_cast<unsigned*>(tn + a.L);
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < a.L; ++k) { ic[k] = 0; tn[k] = clock_next(a, s, k, 0u, 0.0, flags + k); }
+      int m = 1;
+      while (true) {
+        int kb = a.L;
+        double tb = __longlong_as_double(0x7ff0000000000000ll);
+        for (int k = 0; k < a.L; ++k)
+          if (tn[k] < tb) { tb = tn[k]; kb = k; }
+        while (m <= a.M && tb > clock_snap_time(a, m)) ++m;
+        if (m > a.M) break;
+        if ((long long)cnt < cap) {
+          buf[4 * cnt] = m; buf[4 * cnt + 1] = kb; buf[4 * cnt + 2] = flags[kb]; buf[4 * cnt + 3] = 0;
+        }
+        ++cnt;
+        ic[kb] += 1;
+        tn[kb] = clock_next(a, s, kb, ic[kb], tn[kb], flags + kb);
+      }
+      *count = cnt;
+    }
+    return;
+  }
   for (long long j = 1; j <= a.run_steps; ++j) {
     for (int k = threadIdx.x; k < a.L; k += blockDim.x) flags[k] = (unsigned char)draw_gate(a, s, j, k);
     __syncthreads();
@@ -70,7 +96,10 @@ __global__ void export_circuit_kernel(const __grid_constant__ KArgs a, unsigned 
 
 cudaError_t launch_export_circuit(const KArgs& a, unsigned long long s, int* buf, long long cap,
                                   unsigned long long* count, cudaStream_t st) {
-  export_circuit_kernel<<<1, 256, (size_t)a.L, st>>>(a, s, buf, cap, count);
+  const size_t smem = a.variant == 3 ? (size_t)((a.L + 15) / 16) * 16 + (size_t)a.L * 12 : (size_t)a.L;
+  cudaError_t e = cudaFuncSetAttribute(export_circuit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  export_circuit_kernel<<<1, 256, smem, st>>>(a, s, buf, cap, count);
   return cudaGetLastError();
 }
 

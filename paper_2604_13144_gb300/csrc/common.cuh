@@ -58,6 +58,7 @@ struct TermDev {
   int pad;
   unsigned long long thr_event;  // gate (j,k) is not A when x0 < thr_event
   unsigned long long thr_c;      // ... and is C when x1 < thr_c
+  double lam;     // N -> infinity sampler: rate of the term's events per unit time
   double g[32];   // gate of setting B (or the Trotter gate): 4x4 complex row-major,
                   // basis |s_a s_b>, (re,im) interleaved; kind 0 uses g[0..7] as 2x2.
 };
@@ -84,6 +85,7 @@ struct KArgs {
   int n, L, M, n_obs, chi_cap, periodic, variant, max_sweeps;
   long long N, run_steps, n_samples, sample_offset;
   unsigned long long seed;
+  double t_run;              // N -> infinity sampler: evolved time; snapshot m at t_run * m / M
   double cutoff, floor_rel, tol, gap_rel;
   const TermDev* terms;
   const int* snaps;          // [M] snapshot steps
@@ -115,10 +117,13 @@ enum : int { ST_OK = 0, ST_BAD_DIM = 1, ST_BAD_RANK = 2, ST_NONFINITE = 3, ST_CO
 __host__ __device__ inline size_t align_up(size_t x, size_t al) { return (x + al - 1) / al * al; }
 
 // Fixed shared-memory bytes of the engine for (n, L, cap, sizeof complex).
-__host__ __device__ inline size_t smem_fixed_bytes(int n, int L, int cap, int csize) {
+// n_clocks: terms with a Poisson clock (the N -> infinity sampler), else 0.
+__host__ __device__ inline size_t smem_fixed_bytes(int n, int L, int n_clocks, int cap, int csize) {
   size_t b = 0;
   b += align_up((size_t)(n + 1) * 4, 16);          // dims
   b += align_up((size_t)L, 16);                     // flags
+  b += align_up((size_t)n_clocks * 8, 16);          // next event time per term
+  b += align_up((size_t)n_clocks * 4, 16);          // events drawn per term
   b += 64 * 8;                                      // red
   b += 32;                                          // mbarriers of the bulk copies (3 slots)
   b += align_up((size_t)2 * cap * 8, 16);           // wn

@@ -211,6 +211,8 @@ __device__ __forceinline__ cplx<R> ldcg_c(const cplx<R>* p) {
 struct SmemLayout {
   int* dims;          // [n+1]
   unsigned char* flags;  // [L]
+  double* tnext;      // [L] next event time per term (N -> infinity sampler only)
+  unsigned* tcnt;     // [L] events drawn per term (N -> infinity sampler only)
   double* red;        // [64]
   unsigned long long* mbar;  // mbarrier of the bulk copies
   double* wn;         // [2*cap] squared column norms

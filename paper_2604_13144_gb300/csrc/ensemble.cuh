@@ -454,11 +454,65 @@ __device__ __forceinline__ int draw_gate(const KArgs& a, unsigned long long s, l
   return 0;
 }
 
+// The N -> infinity sampler: event i (from 0) of term k in global sample s
+// comes a waiting time -ln(u) / lam_k after time t, with u = ((x0 >> 11) + 1)
+// 2^-53 in (0, 1] from Philox4x64-10 counter (k, i, 1, 0) under key (seed, s);
+// *ev is set to 2 (C) when x1 < floor(r_inf 2^64), else 1 (B). A term with
+// lam_k = 0 never fires: its next time is +infinity.
+__device__ __forceinline__ double clock_next(const KArgs& a, unsigned long long s, int k, unsigned i, double t,
+                                             unsigned char* ev) {
+  const TermDev& T = a.terms[k];
+  if (!(T.lam > 0.0)) {
+    *ev = 1;
+    return __longlong_as_double(0x7ff0000000000000ll);
+  }
+  const u64x4 x = philox4x64_10(u64x4{(unsigned long long)k, (unsigned long long)i, 1ull, 0ull}, a.seed, s);
+  const double u = ((double)(x.x0 >> 11) + 1.0) * 0x1p-53;
+  *ev = x.x1 < T.thr_c ? 2 : 1;
+  return t + (-log(u) / T.lam);
+}
+
+// Snapshot time t_m = t_run m / M (m from 1) of the N -> infinity sampler.
+__device__ __forceinline__ double clock_snap_time(const KArgs& a, int m) {
+  return a.t_run * (double)m / (double)a.M;
+}
+
+// The term whose next event comes first, ties to the lower index; L when no
+// term fires. Called by all threads of the CTA, returns the same to all;
+// red holds 2 x 32 doubles of scratch.
+__device__ __forceinline__ int clock_argmin(const double* tn, int L, double* red) {
+  const int t = threadIdx.x, nw = blockDim.x >> 5;
+  double bt = __longlong_as_double(0x7ff0000000000000ll);
+  int bk = L;
+  for (int k = t; k < L; k += blockDim.x)
+    if (tn[k] < bt) { bt = tn[k]; bk = k; }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const double ot = __shfl_down_sync(0xffffffffu, bt, off);
+    const int ok = __shfl_down_sync(0xffffffffu, bk, off);
+    if (ot < bt || (ot == bt && ok < bk)) { bt = ot; bk = ok; }
+  }
+  if ((t & 31) == 0) { red[t >> 5] = bt; red[32 + (t >> 5)] = (double)bk; }
+  __syncthreads();
+  bt = red[0];
+  bk = (int)red[32];
+  for (int w = 1; w < nw; ++w) {
+    const double ot = red[w];
+    const int ok = (int)red[32 + w];
+    if (ot < bt || (ot == bt && ok < bk)) { bt = ot; bk = ok; }
+  }
+  __syncthreads();
+  return bk;
+}
+
 __device__ inline SmemLayout carve_smem(unsigned char* base, const KArgs& a, int csize) {
   SmemLayout s;
   size_t o = 0;
   s.dims = reinterpret_cast<int*>(base + o); o += align_up((size_t)(a.n + 1) * 4, 16);
   s.flags = base + o; o += align_up((size_t)a.L, 16);
+  const int nclk = a.variant == 3 ? a.L : 0;
+  s.tnext = reinterpret_cast<double*>(base + o); o += align_up((size_t)nclk * 8, 16);
+  s.tcnt = reinterpret_cast<unsigned*>(base + o); o += align_up((size_t)nclk * 4, 16);
   s.red = reinterpret_cast<double*>(base + o); o += 64 * 8;
   s.mbar = reinterpret_cast<unsigned long long*>(base + o); o += 32;
   s.wn = reinterpret_cast<double*>(base + o); o += align_up((size_t)2 * a.chi_cap * 8, 16);
@@ -470,6 +524,46 @@ __device__ inline SmemLayout carve_smem(unsigned char* base, const KArgs& a, int
   o = align_up(o, 128);
   s.x = base + o;
   return s;
+}
+
+// One sample of the N -> infinity sampler: the events of all terms merged in
+// time order; snapshot m is taken once the next event lies beyond t_m.
+template <typename R>
+__device__ __noinline__ void run_continuous(Engine<R>& eng, const KArgs& a, const SmemLayout& sm, long long si,
+                                            unsigned long long s) {
+  int sign_count = 0;
+  int mi = 0;
+  {
+    PhaseTimer pt(eng.st, PH_SAMPLER);
+    for (int k = threadIdx.x; k < a.L; k += blockDim.x) {
+      sm.tcnt[k] = 0;
+      sm.tnext[k] = clock_next(a, s, k, 0u, 0.0, sm.flags + k);
+    }
+    __syncthreads();
+  }
+  while (true) {
+    int k;
+    {
+      PhaseTimer pt(eng.st, PH_SAMPLER);
+      k = clock_argmin(sm.tnext, a.L, sm.red);
+    }
+    const double tk = k < a.L ? sm.tnext[k] : __longlong_as_double(0x7ff0000000000000ll);
+    while (mi < a.M && tk > clock_snap_time(a, mi + 1)) {
+      if (a.obs_ops) eng.measure_strings(a.v + ((size_t)si * a.M + mi) * a.n_obs);
+      else eng.measure_z(a.v + ((size_t)si * a.M + mi) * a.n_obs);
+      if (threadIdx.x == 0) a.sign[(size_t)si * a.M + mi] = (sign_count & 1) ? -1 : 1;
+      ++mi;
+    }
+    if (mi >= a.M) break;
+    eng.apply_event(k, sm.flags[k], sign_count);
+    __syncthreads();
+    if (eng.failed()) break;
+    if (threadIdx.x == 0) {
+      const unsigned i = ++sm.tcnt[k];
+      sm.tnext[k] = clock_next(a, s, k, i, sm.tnext[k], sm.flags + k);
+    }
+    __syncthreads();
+  }
 }
 
 template <typename R>
@@ -499,6 +593,11 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
     }
     int sign_count = 0;
     int mi = 0;
+    if (a.variant == 3) {
+      run_continuous(eng, a, sm, si, s);
+      if (a.state_out && si == 0 && !eng.failed()) eng.export_state(a.state_out, a.state_dims);
+      continue;
+    }
     for (long long j = 1; j <= a.run_steps; ++j) {
       {
         PhaseTimer pt(eng.st, PH_SAMPLER);

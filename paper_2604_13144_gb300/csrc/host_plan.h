@@ -39,8 +39,9 @@ struct PlanT {
   Vec<unsigned char> bits;
   Vec<unsigned char> obs_ops;   // Pauli-string observables: [n_obs][n] codes in chain order
   double gnorm_step = 1.0, expected_nu = 0.0;
+  double t_run = 0.0;           // N -> infinity sampler: evolved time T run_steps / N
   void reset() {
-    n = L = M = n_obs = periodic = 0; N = run_steps = 0; gnorm_step = 1.0; expected_nu = 0.0;
+    n = L = M = n_obs = periodic = 0; N = run_steps = 0; gnorm_step = 1.0; expected_nu = 0.0; t_run = 0.0;
     terms.clear(); snaps.clear(); gnorm.clear(); obs.clear(); bits.clear(); obs_ops.clear();
   }
   bool overflowed() const;
@@ -131,7 +132,8 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   if (!(std::isfinite(Q->T) && Q->T >= 0.0) || Q->n_steps < 1) return TEPAI_ERR_INVALID_ARG;
   if (!(std::isfinite(Q->delta) && Q->delta > 0.0)) return TEPAI_ERR_INVALID_ARG;
   if (Q->chi_max < 1 || !(std::isfinite(Q->cutoff) && Q->cutoff >= 0.0)) return TEPAI_ERR_INVALID_ARG;
-  if (Q->variant < 0 || Q->variant > 2 || Q->precision < 0 || Q->precision > 1) return TEPAI_ERR_INVALID_ARG;
+  if (Q->variant < 0 || Q->variant > 3 || Q->precision < 0 || Q->precision > 1) return TEPAI_ERR_INVALID_ARG;
+  if (Q->variant == TEPAI_CONTINUOUS && !(Q->delta < M_PI)) return TEPAI_ERR_INVALID_ARG;
   if (Q->launch_variant < 0 || Q->launch_variant > 6) return TEPAI_ERR_INVALID_ARG;
   if (Q->n_samples < 0 || Q->sample_offset < 0) return TEPAI_ERR_INVALID_ARG;
   const long long S = Q->run_steps ? Q->run_steps : Q->n_steps;
@@ -172,7 +174,13 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   struct T0 { int kind, a, b, pauli; double c; };
   hp.L = n + 3 * nb;
   const double delta = Q->delta;
-  double sumq = 0.0, gstep = 1.0;
+  const bool cont = Q->variant == TEPAI_CONTINUOUS;
+  // N -> infinity limit of the draw probabilities built from Eq. gammas: the
+  // rate of "not A" per unit time is |c_k| (3 - cos Delta) / sin Delta, the
+  // share of C among those events (1 - cos Delta) / (3 - cos Delta).
+  const double rate = cont ? (3.0 - std::cos(delta)) / std::sin(delta) : 0.0;
+  const double r_inf = cont ? (1.0 - std::cos(delta)) / (3.0 - std::cos(delta)) : 0.0;
+  double sumq = 0.0, gstep = 1.0, c1 = 0.0, sumlam = 0.0;
   for (int k = 0; k < hp.L; ++k) {
     T0 t;
     if (k < n) {
@@ -186,7 +194,14 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
     td.kind = t.kind; td.a = t.a; td.b = t.b; td.pauli = t.pauli;
     const double th = 2.0 * t.c * Q->T / (double)Q->n_steps;
     double q, r, gn, phi;
-    if (Q->variant == TEPAI_TROTTER) {
+    td.lam = 0.0;
+    if (cont) {
+      q = 0.0; r = r_inf; gn = 1.0;
+      phi = t.c != 0.0 ? std::copysign(delta, t.c) : delta;
+      td.lam = std::fabs(t.c) * rate;
+      c1 += std::fabs(t.c);
+      sumlam += td.lam;
+    } else if (Q->variant == TEPAI_TROTTER) {
       q = 1.0; r = 0.0; gn = 1.0; phi = th;
     } else {
       if (std::fabs(th) > delta || delta > M_PI) return TEPAI_ERR_THETA_EXCEEDS_DELTA;
@@ -223,6 +238,22 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   }
   hp.gnorm_step = gstep;
   hp.expected_nu = (double)S * sumq;
+  if (cont) {
+    // snapshot m at t_m = t_run m / M, with ||g(t_m)||_1 of Eq. overhead
+    hp.t_run = Q->T * (double)S / (double)Q->n_steps;
+    hp.gnorm_step = 1.0;
+    hp.expected_nu = sumlam * hp.t_run;
+    // every sample runs about expected_nu events in one CTA: refuse problems
+    // whose samples would not end in reasonable time
+    if (!(hp.expected_nu <= 1e7)) return TEPAI_ERR_INVALID_ARG;
+    for (int m = 1; m <= hp.M; ++m) {
+      const double tm = hp.t_run * (double)m / (double)hp.M;
+      hp.snaps.push_back(m);
+      hp.gnorm.push_back(std::exp(2.0 * std::tan(delta / 2) * c1 * tm));
+    }
+    if (hp.overflowed()) return TEPAI_ERR_INVALID_ARG;
+    return TEPAI_OK;
+  }
   for (int m = 1; m <= hp.M; ++m) {
     const long long j = (long long)m * S / hp.M;
     hp.snaps.push_back((int)j);
@@ -252,9 +283,9 @@ struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems, per_s
 // bond dimensions run several samples per SM. 0 (or a variant that does not
 // apply) keeps the rule.
 template <class Occ>
-inline cudaError_t choose_launch_shape(int n, int L, int cap, int csize, int optin, Occ occ, LaunchShape& ls,
-                                       int variant = 0) {
-  const size_t fixed = smem_fixed_bytes(n, L, cap, csize);
+inline cudaError_t choose_launch_shape(int n, int L, int n_clocks, int cap, int csize, int optin, Occ occ,
+                                       LaunchShape& ls, int variant = 0) {
+  const size_t fixed = smem_fixed_bytes(n, L, n_clocks, cap, csize);
   const size_t xbytes = (size_t)4 * cap * cap * csize;
   int per_sm = 1;
   cudaError_t e;

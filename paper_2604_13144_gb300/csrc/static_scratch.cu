@@ -93,7 +93,7 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
                                       : occupancy_ensemble_f32(blk, sm_bytes, per);
   };
   LaunchShape ls{};
-  if (choose_launch_shape(hp.n, hp.L, cap, csize, optin, occ, ls, Q->launch_variant) != cudaSuccess)
+  if (choose_launch_shape(hp.n, hp.L, Q->variant == TEPAI_CONTINUOUS ? hp.L : 0, cap, csize, optin, occ, ls, Q->launch_variant) != cudaSuccess)
     return TEPAI_ERR_CUDA;
   const int block = ls.block, x_elems = ls.x_elems, x_in_smem = ls.x_in_smem, per_sm = ls.per_sm;
   const size_t smem = ls.smem;
@@ -115,7 +115,7 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
   a.periodic = hp.periodic; a.variant = Q->variant;
   a.max_sweeps = Q->precision == TEPAI_FP64 ? 60 : 40;
   a.N = hp.N; a.run_steps = hp.run_steps; a.n_samples = Q->n_samples; a.sample_offset = Q->sample_offset;
-  a.seed = Q->seed; a.cutoff = Q->cutoff;
+  a.seed = Q->seed; a.t_run = hp.t_run; a.cutoff = Q->cutoff;
   a.floor_rel = Q->precision == TEPAI_FP64 ? 1e-14 : 4e-6;
   a.tol = Q->precision == TEPAI_FP64 ? 2 * 1.1102230246251565e-16 : 2 * 5.9604644775390625e-08;
   a.gap_rel = 1e-4;

@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtepai.so")
 
-TEPAI_UNBIASED, TEPAI_NO_PI, TEPAI_TROTTER = 0, 1, 2
+TEPAI_UNBIASED, TEPAI_NO_PI, TEPAI_TROTTER, TEPAI_CONTINUOUS = 0, 1, 2, 3
 TEPAI_FP64, TEPAI_MIXED = 0, 1
 
 EXPORTED = ["tepai_create", "tepai_destroy", "tepai_run", "tepai_sample_values",

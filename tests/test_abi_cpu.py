@@ -74,3 +74,28 @@ def test_no_pi_gnorm_is_one(T):
     prob, par, _ = W.config(2)
     g, _ = T.tepai_gnorm(prob, W.Params(**{**par.__dict__, "variant": 1}))
     assert np.all(np.abs(g - 1.0) < 1e-15)
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_continuous_host_planner_matches_oracle(T, cfg):
+    """N -> infinity sampler: ||g(t_m)||_1 and E[nu] from the host planner equal
+    the oracle's to rounding (the oracle sums ||c||_1 with Python's compensated
+    sum, the planner plainly); small Delta is no obstacle (no theta <= Delta
+    bound), Delta >= pi and runaway event counts are refused."""
+    prob, par, _ = W.config(cfg)
+    cp = W.Params(**{**par.__dict__, "n_steps": 10, "n_snapshots": 5, "variant": 3})
+    g, nu = T.tepai_gnorm(prob, cp)
+    plan = planner.make_plan(prob, cp.T, cp.n_steps, cp.delta, planner.CONTINUOUS)
+    ts = planner.snapshot_times(plan, cp.steps_run(), cp.n_snapshots)
+    want = np.array([planner.gnorm_time(plan, t) for t in ts])
+    assert np.allclose(g, want, rtol=1e-14, atol=0)
+    assert abs(nu / (np.sum(plan.lam) * ts[-1]) - 1) < 1e-14
+    assert abs(nu / planner.nu_infinity(prob, cp.T, cp.delta) - 1) < 1e-14
+    for bad in (W.Params(**{**cp.__dict__, "delta": math.pi}),
+                W.Params(**{**cp.__dict__, "delta": 1e-9})):     # ~1e10 events per sample
+        with pytest.raises(T.TepaiError) as e:
+            T.tepai_gnorm(prob, bad)
+        assert e.value.code == 1
+    bad = W.Params(**{**cp.__dict__, "variant": 4})
+    with pytest.raises(T.TepaiError):
+        T.tepai_gnorm(prob, bad)
