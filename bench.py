@@ -191,6 +191,11 @@ def tts_config1(T, W, torch, local, subset=16):
         for s in range(subset):
             T.tepai_run(ctx, prob, W.Params(**{**par.__dict__, "n_samples": 1, "sample_offset": s}))
         t_one = (time.perf_counter() - t) / subset * par.n_samples
+        # the same ensemble drawn in the N -> infinity limit (no Trotter error)
+        cont = W.Params(**{**mixed.__dict__, "variant": T.TEPAI_CONTINUOUS})
+        t = time.perf_counter()
+        rc = T.tepai_run(ctx, prob, cont)
+        t_cont = time.perf_counter() - t
     finally:
         T.tepai_destroy(ctx)
     err = float(abs(rm["mean"] - rf["mean"]).max())
@@ -199,7 +204,11 @@ def tts_config1(T, W, torch, local, subset=16):
             "fp64_one_sample_per_launch_s": t_one, "one_per_launch_subset": subset,
             "speedup_vs_fp64_one_per_launch": t_one / t_mixed,
             "max_abs_err_mixed_vs_fp64": err,
-            "stderr_fp64": float(rf["stderr"].max())}
+            "stderr_fp64": float(rf["stderr"].max()),
+            "mixed_continuous_s": t_cont,
+            "events_per_sample_finite_n": rm["stats"]["events"] / par.n_samples,
+            "events_per_sample_continuous": rc["stats"]["events"] / par.n_samples,
+            "max_abs_diff_continuous_vs_finite_n": float(abs(rc["mean"] - rm["mean"]).max())}
 
 
 # ---------------------------------------------------------------- our arm
