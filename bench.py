@@ -208,6 +208,10 @@ def tts_config1(T, W, torch, local, subset=16):
             "mixed_continuous_s": t_cont,
             "events_per_sample_finite_n": rm["stats"]["events"] / par.n_samples,
             "events_per_sample_continuous": rc["stats"]["events"] / par.n_samples,
+            "sampler_phase_share_continuous": rc["stats"]["phase_cycles"]["sampler"]
+            / max(1.0, float(sum(rc["stats"]["phase_cycles"].values()))),
+            "sampler_phase_share_finite_n": rm["stats"]["phase_cycles"]["sampler"]
+            / max(1.0, float(sum(rm["stats"]["phase_cycles"].values()))),
             "max_abs_diff_continuous_vs_finite_n": float(abs(rc["mean"] - rm["mean"]).max())}
 
 
