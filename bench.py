@@ -264,8 +264,10 @@ def run_ours(a):
     phases, subphases = {}, {}
     grid = 1
     nconv, maxchi = 0, 0
+    order_on = 0
     for i in range(a.steps):
         ms, st = step(a.warmup + i)
+        order_on = st["sample_order"]
         kms += ms
         upd += st["gate_updates"] + st["swap_updates"]
         flops += st["alg_flops"]
@@ -331,7 +333,9 @@ def run_ours(a):
                    "l2": "inputs larger than L2 (per-CTA MPS arenas, GBs)"},
         "e2e": {"value": e2e_u / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 2 * a.steps,
+        # per step: the ensemble kernel and the reduction, plus the sample-cost
+        # and ordering kernels when the call hands out samples costliest first
+        "gpu_launches": (2 + 2 * order_on) * a.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,

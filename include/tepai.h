@@ -134,7 +134,8 @@ typedef struct {
     int device_status[3];          /* first device check failure: (code, detail, CTA); code 0 =
                                       none, 1 bond dimension out of range, 2 invalid singular-value
                                       ranking, 3 non-finite column norm, 4 bulk copy did not land,
-                                      5 Jacobi column handoff did not arrive */
+                                      5 Jacobi column handoff did not arrive, 6 invalid entry in
+                                      the sample order */
     double phase_cycles[8];        /* SM cycles per phase, summed over CTAs: init, sampler,
                                       single-site gates, theta, Jacobi SVD, truncation and
                                       write-back, centre moves (QR), measurement */
@@ -145,6 +146,11 @@ typedef struct {
                                       panels, trailing block-reflector updates, explicit Q, R times
                                       the neighbour site, SVD projection and write-back, waits on
                                       bulk copies, Jacobi passes, singular-value ranking */
+    int sample_order;              /* 1 when the call handed out its samples costliest first
+                                      (predicted two-site updates, from the sampler's own draws):
+                                      sampled variants, more samples than CTAs, at most 65536
+                                      draws per sample, unless TEPAI_LPT=0. Adds two small
+                                      launches per call; results do not depend on it. */
 } tepai_stats;
 
 /* Circuit event of one sample: Trotter step j (1-based), term k, setting v

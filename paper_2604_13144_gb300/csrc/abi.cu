@@ -25,6 +25,8 @@ cudaError_t launch_signed_reduce(const double* v, const signed char* sign, long 
                                  const double* gnorm, double* mean, double* se, double* part, cudaStream_t st);
 cudaError_t launch_export_circuit(const KArgs& a, unsigned long long s, int* buf, long long cap,
                                   unsigned long long* count, cudaStream_t st);
+cudaError_t launch_order_samples(const KArgs& a, cudaStream_t st);
+const void* sample_cost_kernel_fn();
 }  // namespace tepai
 
 using namespace tepai;
@@ -51,6 +53,17 @@ NumCfg num_cfg(int precision) {
   return {2 * 5.9604644775390625e-08, 4e-6, 1e-4, 40, 8};
 }
 
+// Longest-first sample order: on unless TEPAI_LPT=0 (kept switchable for A/B
+// timing). It applies to sampled variants whose samples are short (at most
+// 65536 draws each), where the persistent grid's last wave is a visible share
+// of a call, and only when there are more samples than CTAs.
+bool lpt_applies(const HostPlan& hp, const tepai_params* Q, int grid) {
+  const char* e = std::getenv("TEPAI_LPT");
+  if (e && e[0] == '0' && e[1] == 0) return false;
+  if (Q->variant != TEPAI_UNBIASED && Q->variant != TEPAI_NO_PI) return false;
+  return hp.run_steps * (long long)hp.L <= 65536 && Q->n_samples > grid && Q->n_samples < (1LL << 31);
+}
+
 // QR preconditioning of the Jacobi SVD: on unless TEPAI_JACOBI_PRECONDITION=0
 // (kept switchable for A/B timing of the two SVD variants).
 int jacobi_precondition() {
@@ -60,7 +73,7 @@ int jacobi_precondition() {
 
 struct Layout {
   size_t terms, snaps, gnorm, obs, bits, dims, init, canon_meta, stats, counter, status, v, sign, arena, stride,
-      canon, ops, total;
+      canon, ops, cost, order, total;
 };
 
 Layout layout(const HostPlan& hp, const tepai_params* Q, int grid, bool has_init, size_t init_elems) {
@@ -81,6 +94,8 @@ Layout layout(const HostPlan& hp, const tepai_params* Q, int grid, bool has_init
   L.status = o; o = al256(o + 4 * sizeof(int));
   L.v = o; o = al256(o + sizeof(double) * (size_t)Q->n_samples * hp.M * hp.n_obs);
   L.sign = o; o = al256(o + (size_t)Q->n_samples * hp.M);
+  L.cost = o; o = al256(o + sizeof(int) * (size_t)Q->n_samples);
+  L.order = o; o = al256(o + sizeof(int) * (size_t)Q->n_samples);
   L.stride = al256(((size_t)hp.n * 2 * cap * cap + 8 * cap * cap) * nc.csize);
   L.arena = o; o = al256(o + L.stride * (size_t)grid);
   // one more arena slot for the canonical form of a shared start state
@@ -101,6 +116,7 @@ struct GraphState {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t kernel = nullptr;
+  cudaGraphNode_t cost_kernel = nullptr;   // the sample-cost launch, when the order is on
   const void* outs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaStream_t stream = nullptr;     // the caller's stream of the capture
   cudaStream_t own = nullptr;        // capture / launch stream when the caller's is a default stream
@@ -221,6 +237,10 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   a.stats = reinterpret_cast<DevStats*>(base + L.stats);
   a.counter = reinterpret_cast<unsigned long long*>(base + L.counter);
   a.status = reinterpret_cast<int*>(base + L.status);
+  if (lpt_applies(hp, Q, ls.grid)) {
+    a.cost = reinterpret_cast<int*>(base + L.cost);
+    a.order = reinterpret_cast<const int*>(base + L.order);
+  }
   a.x_in_smem = ls.x_in_smem; a.smem_x_elems = ls.x_elems;
   a.precondition = jacobi_precondition();
   if (init) {
@@ -255,6 +275,7 @@ cudaError_t enqueue_execute(const Prepared& pr, double* d_mean, double* d_se, do
   if ((e = cudaMemsetAsync(a.stats, 0, sizeof(DevStats), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.status, 0, 4 * sizeof(int), st)) != cudaSuccess) return e;
+  if (a.order && (e = launch_order_samples(a, st)) != cudaSuccess) return e;
   if (capturing)
     e = pr.precision == TEPAI_FP64 ? launch_ensemble_captured_f64(a, pr.grid, pr.block, pr.smem, st)
                                    : launch_ensemble_captured_f32(a, pr.grid, pr.block, pr.smem, st);
@@ -300,19 +321,22 @@ cudaError_t capture_execute(Prepared& pr, double* d_mean, double* d_se, double* 
   if ((e = cudaGraphGetNodes(graph, nullptr, &nn)) != cudaSuccess) { cudaGraphDestroy(graph); return e; }
   std::vector<cudaGraphNode_t> nodes(nn);
   if (nn && (e = cudaGraphGetNodes(graph, nodes.data(), &nn)) != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  cudaGraphNode_t kn = nullptr;
+  cudaGraphNode_t kn = nullptr, cn = nullptr;
   for (cudaGraphNode_t nd : nodes) {
     cudaGraphNodeType ty;
     if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
     cudaKernelNodeParams p{};
-    if (cudaGraphKernelNodeGetParams(nd, &p) == cudaSuccess && p.func == fn) kn = nd;
+    if (cudaGraphKernelNodeGetParams(nd, &p) != cudaSuccess) continue;
+    if (p.func == fn) kn = nd;
+    if (p.func == sample_cost_kernel_fn()) cn = nd;
   }
-  if (!kn) { cudaGraphDestroy(graph); return cudaErrorInvalidValue; }
+  if (!kn || (pr.ka.order && !cn)) { cudaGraphDestroy(graph); return cudaErrorInvalidValue; }
   cudaGraphExec_t exec = nullptr;
   if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) { cudaGraphDestroy(graph); return e; }
   pr.g.graph = graph;
   pr.g.exec = exec;
   pr.g.kernel = kn;
+  pr.g.cost_kernel = cn;
   pr.g.outs[0] = d_mean; pr.g.outs[1] = d_se; pr.g.outs[2] = d_part; pr.g.outs[3] = d_v; pr.g.outs[4] = d_sign;
   pr.g.stream = st;
   pr.g.offset = pr.ka.sample_offset;
@@ -345,13 +369,18 @@ int execute_impl(void* ws, double* d_mean, double* d_se, double* d_part, double*
       CK(ce);
     }
   } else if (pr.g.offset != pr.ka.sample_offset) {
-    cudaKernelNodeParams p{};
-    CK(cudaGraphKernelNodeGetParams(pr.g.kernel, &p));
+    // both kernels that draw samples take the arguments with the new offset
     KArgs ka = pr.ka;
     void* args[1] = {&ka};
-    p.kernelParams = args;
-    p.extra = nullptr;
-    CK(cudaGraphExecKernelNodeSetParams(pr.g.exec, pr.g.kernel, &p));
+    cudaGraphNode_t nodes[2] = {pr.g.kernel, pr.g.cost_kernel};
+    for (cudaGraphNode_t nd : nodes) {
+      if (!nd) continue;
+      cudaKernelNodeParams p{};
+      CK(cudaGraphKernelNodeGetParams(nd, &p));
+      p.kernelParams = args;
+      p.extra = nullptr;
+      CK(cudaGraphExecKernelNodeSetParams(pr.g.exec, nd, &p));
+    }
     pr.g.offset = pr.ka.sample_offset;
   }
   if (pr.g.own) {
@@ -401,6 +430,7 @@ int stats_impl(void* ws, tepai_stats* out, cudaStream_t st) {
   out->jacobi_pairs = (double)ds.jac_pairs;
   out->jacobi_rotations = (double)ds.jac_rots;
   for (int p = 0; p < SP_N; ++p) out->subphase_cycles[p] = (double)ds.sub_cycles[p];
+  out->sample_order = pr.ka.order ? 1 : 0;
   return TEPAI_OK;
 }
 

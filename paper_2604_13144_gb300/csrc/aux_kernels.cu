@@ -44,6 +44,76 @@ cudaError_t launch_signed_reduce(const double* v, const signed char* sign, long 
   return cudaGetLastError();
 }
 
+// Predicted cost of every sample of the call, for longest-first scheduling:
+// its two-site updates, 1 per B event of a bond gate whose sites are adjacent
+// in the chain and 3 (swap, gate, swap back) when they are two apart. Z and C
+// events need no SVD and cost 0. One warp per sample; the lanes split the
+// (step, term) draws, which are the kernel's own draws.
+constexpr int kCostBuckets = 4096;
+
+__global__ void sample_cost_kernel(const __grid_constant__ KArgs a) {
+  const long long q = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= a.n_samples) return;
+  const unsigned long long s = (unsigned long long)(a.sample_offset + q);
+  const long long draws = a.run_steps * (long long)a.L;
+  int c = 0;
+  for (long long e = lane; e < draws; e += 32) {
+    const long long j = 1 + e / a.L;
+    const int k = (int)(e - (j - 1) * a.L);
+    if (draw_gate(a, s, j, k) == 1) {
+      const TermDev& T = a.terms[k];
+      if (T.kind == 1) c += (T.b - T.a == 1) ? 1 : 3;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+  if (lane == 0) a.cost[q] = c < kCostBuckets - 1 ? c : kCostBuckets - 1;
+}
+
+// order[0..n) = the samples by decreasing cost: a counting sort in one CTA
+// (the order within one cost is left to the atomics; results do not depend
+// on it, since every sample writes only its own outputs).
+__global__ void order_by_cost_kernel(const int* __restrict__ cost, int* __restrict__ order, long long n) {
+  __shared__ int pos[kCostBuckets];
+  for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) pos[b] = 0;
+  __syncthreads();
+  for (long long q = threadIdx.x; q < n; q += blockDim.x) {
+    int c = cost[q];
+    c = c < 0 ? 0 : (c >= kCostBuckets ? kCostBuckets - 1 : c);
+    atomicAdd(&pos[c], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // exclusive prefix from the highest cost down
+    int run = 0;
+    for (int b = kCostBuckets - 1; b >= 0; --b) {
+      const int h = pos[b];
+      pos[b] = run;
+      run += h;
+    }
+  }
+  __syncthreads();
+  for (long long q = threadIdx.x; q < n; q += blockDim.x) {
+    int c = cost[q];
+    c = c < 0 ? 0 : (c >= kCostBuckets ? kCostBuckets - 1 : c);
+    const int p = atomicAdd(&pos[c], 1);
+    order[p] = (int)q;
+  }
+}
+
+cudaError_t launch_order_samples(const KArgs& a, cudaStream_t st) {
+  const int wpb = 8;
+  const long long blocks = (a.n_samples + wpb - 1) / wpb;
+  sample_cost_kernel<<<(unsigned)blocks, 32 * wpb, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  order_by_cost_kernel<<<1, 1024, 0, st>>>(a.cost, const_cast<int*>(a.order), a.n_samples);
+  return cudaGetLastError();
+}
+
+const void* sample_cost_kernel_fn() { return reinterpret_cast<const void*>(&sample_cost_kernel); }
+
 // Events of one sample in gate order, drawn with the same device sampler as the
 // ensemble kernel. One CTA; thread 0 appends in k order after each step.
 __global__ void export_circuit_kernel(const __grid_constant__ KArgs a, unsigned long long s, int* buf,

@@ -104,6 +104,8 @@ struct KArgs {
   signed char* sign;         // [n_samples][M]
   DevStats* stats;
   unsigned long long* counter;  // work-queue head
+  const int* order;          // [n_samples] queue slot -> sample, costliest first; nullptr = identity
+  int* cost;                 // [n_samples] predicted two-site updates per sample (when order is set)
   int x_in_smem;             // the SVD working matrix lives in shared memory
   int smem_x_elems;          // capacity of that buffer (complex elements)
   int* status;               // [4]: first failure (code, detail, sample, 0); 0 = ok
@@ -112,7 +114,8 @@ struct KArgs {
 
 // Device status codes. A CTA that detects a broken invariant records the first
 // failure, touches no more memory for that sample, and leaves the kernel.
-enum : int { ST_OK = 0, ST_BAD_DIM = 1, ST_BAD_RANK = 2, ST_NONFINITE = 3, ST_COPY_TIMEOUT = 4, ST_HANDOFF_TIMEOUT = 5 };
+enum : int { ST_OK = 0, ST_BAD_DIM = 1, ST_BAD_RANK = 2, ST_NONFINITE = 3, ST_COPY_TIMEOUT = 4, ST_HANDOFF_TIMEOUT = 5,
+             ST_BAD_ORDER = 6 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t al) { return (x + al - 1) / al * al; }
 

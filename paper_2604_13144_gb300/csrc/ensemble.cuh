@@ -579,10 +579,24 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
   }
   __syncthreads();
   while (!eng.failed()) {
-    if (threadIdx.x == 0) s_next = (long long)atomicAdd(a.counter, 1ull);
+    if (threadIdx.x == 0) {
+      // queue slot -> sample: with an order, the costliest samples go first
+      // (longest-processing-time-first), so the grid ends on short samples
+      const long long q = (long long)atomicAdd(a.counter, 1ull);
+      long long si = q;
+      if (a.order && q < a.n_samples) {
+        si = a.order[q];
+        if (si < 0 || si >= a.n_samples) si = -1;
+      }
+      s_next = si;
+    }
     __syncthreads();
     const long long si = s_next;
     __syncthreads();
+    if (si < 0) {
+      eng.fail(ST_BAD_ORDER, 0);
+      break;
+    }
     if (si >= a.n_samples) break;
     const unsigned long long s = (unsigned long long)(a.sample_offset + si);
     {

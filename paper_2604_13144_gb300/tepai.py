@@ -61,7 +61,8 @@ class Stats(C.Structure):
                 ("max_chi", C.c_int), ("n_not_converged", C.c_int),
                 ("device_status", C.c_int * 3), ("phase_cycles", C.c_double * 8),
                 ("grid_ctas", C.c_int), ("jacobi_pairs", C.c_double),
-                ("jacobi_rotations", C.c_double), ("subphase_cycles", C.c_double * 8)]
+                ("jacobi_rotations", C.c_double), ("subphase_cycles", C.c_double * 8),
+                ("sample_order", C.c_int)]
 
     PHASES = ("init", "sampler", "single_site", "theta", "jacobi", "truncate", "qr", "measure")
     SUBPHASES = ("qr_panel", "qr_apply", "qr_formq", "qr_rmul", "projection", "bulk_wait",

@@ -275,3 +275,38 @@ def test_bench_workload_sampled_parity(T):
         err = float(np.max(np.abs(v[si] - ref["v"][0])))
         assert err <= TOLMIX, (si, err)
         assert sg[si, 0] == ref["sign"][0, 0]
+
+
+def test_longest_first_order_leaves_results_unchanged(T, monkeypatch):
+    """With more samples than CTAs and short samples, the queue hands out the
+    samples costliest first. Every sample still writes only its own outputs, so
+    the values are bit-identical to the plain queue order, also after a graph
+    replay with a new sample offset (both sampling kernels are re-parameterised)."""
+    import torch
+    prob = W.spin_ring(8, 1.0, seed=4)
+    par = P(n_samples=40, precision=1, n_steps=200, n_snapshots=4)
+
+    def run_both(env):
+        if env is None:
+            monkeypatch.delenv("TEPAI_LPT", raising=False)
+        else:
+            monkeypatch.setenv("TEPAI_LPT", env)
+        r = T.DeviceRun(prob, par, grid_ctas=4)
+        out = []
+        for off in (0, 1000):
+            r.set_sample_offset(off)
+            v = torch.zeros((40, 4, 8), dtype=torch.float64, device="cuda")
+            sg = torch.zeros((40, 4), dtype=torch.int8, device="cuda")
+            r.execute(v=v, sign=sg)
+            torch.cuda.synchronize()
+            st = r.stats()
+            assert st["device_status"][0] == 0, st
+            out.append((v.cpu(), sg.cpu(), st["events"]))
+        return out
+
+    lpt = run_both(None)
+    plain = run_both("0")
+    for (va, sa, ea), (vb, sb, eb) in zip(lpt, plain):
+        assert torch.equal(va, vb) and torch.equal(sa, sb) and ea == eb
+        assert torch.count_nonzero(va) > 0
+    assert not torch.equal(lpt[0][0], lpt[1][0])          # the offset took effect
