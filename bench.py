@@ -31,8 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "TE-PAI MPS gate-updates/s at chi=128"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one ensemble_kernel
 # launch of the default workload, divided by the two-site updates of that launch
-# (7.766e12 B over 123751 updates), from one ncu capture of the current kernel.
-DRAM_BYTES_PER_UPDATE = 6.276e7
+# (7.897e12 B over 123751 updates), from one ncu capture of the current kernel.
+DRAM_BYTES_PER_UPDATE = 6.381e7
 UNIT = "updates/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
