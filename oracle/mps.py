@@ -30,6 +30,14 @@ in the natural order.
 - A gate on sites two chain positions apart (p, p+2) swaps positions p+1 and
   p+2, acts on chain bond (p, p+1), and swaps back. Every swap is a two-site
   update with truncation.
+- Alternatively (three_site=True) such a gate is one three-site update: with
+  the centre on p, theta3 = A_p A_{p+1} A_{p+2} takes the gate on its first
+  and third physical indices and is split back left to right by two truncated
+  SVDs, (chi_l 2) x (4 chi_r) and then (k 2) x (2 chi_r), each under the same
+  keep rule and renormalisation; the centre ends on p+2. This is the cheapest
+  form of applying the bond-2 gate as an operator on three sites (a
+  three-site MPO of bond dimension 1 to 4) instead of routing it by swaps; it
+  truncates twice instead of three times.
 - <Z_i> is contracted with left and right environments. This makes no
   canonical-form assumption.
 """
@@ -66,7 +74,7 @@ class MPS:
         self.pos = [0] * len(self.A)
         for p, site in enumerate(self.order):
             self.pos[site] = p
-        self.stats = {"gate_updates": 0, "swap_updates": 0, "qr_moves": 0,
+        self.stats = {"gate_updates": 0, "swap_updates": 0, "three_site_updates": 0, "qr_moves": 0,
                       "max_discarded": 0.0, "max_chi": 1, "min_cut_gap": float("inf")}
 
     @property
@@ -190,6 +198,46 @@ def apply_two(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float,
         move_centre(m, i)
 
 
+def _split(m: MPS, M: np.ndarray, chi_max: int, cutoff: float, floor_rel: float, gap_rel: float):
+    """Truncated SVD of one split of a three-site update: the keep rule of
+    keep_count, kept singular values renormalised to unit norm; returns
+    (U_k, s_k, Vh_k, discarded weight fraction) and records it, the cut gap
+    and k."""
+    U, s, Vh = np.linalg.svd(M, full_matrices=False)
+    k = keep_count(s, chi_max, cutoff, floor_rel, gap_rel)
+    tot = float(np.sum(s ** 2))
+    disc = 0.0 if tot == 0.0 else float(np.sum(s[k:] ** 2)) / tot
+    if k < s.size and s[k] > floor_rel * s[0]:
+        m.stats["min_cut_gap"] = min(m.stats["min_cut_gap"], float((s[k - 1] - s[k]) / s[0]))
+    kept = s[:k] / np.sqrt(np.sum(s[:k] ** 2))
+    m.stats["max_discarded"] = max(m.stats["max_discarded"], disc)
+    m.stats["max_chi"] = max(m.stats["max_chi"], k)
+    return U[:, :k], kept, Vh[:k, :], disc
+
+
+def apply_three(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float, floor_rel: float,
+                gap_rel: float = 1e-4):
+    """Gate g (4x4, basis |s_i s_{i+2}>) on chain positions i and i+2 as one
+    three-site update (see the module notes); the centre ends on i+2.
+    Returns the discarded weight fractions of the two splits."""
+    move_centre(m, i)
+    A, B, C3 = m.A[i], m.A[i + 1], m.A[i + 2]
+    chl, chr_ = A.shape[0], C3.shape[2]
+    th = np.einsum('asc,ctd,dub->astub', A, B, C3)                  # (chl,2,2,2,chr)
+    th = np.einsum('xysu,astub->axtyb', g.reshape(2, 2, 2, 2), th)  # gate on s and u
+    U1, s1, V1, e1 = _split(m, th.reshape(chl * 2, 4 * chr_), chi_max, cutoff, floor_rel, gap_rel)
+    k1 = s1.size
+    m.A[i] = U1.reshape(chl, 2, k1)
+    rest = (s1[:, None] * V1).reshape(k1 * 2, 2 * chr_)
+    U2, s2, V2, e2 = _split(m, rest, chi_max, cutoff, floor_rel, gap_rel)
+    k2 = s2.size
+    m.A[i + 1] = U2.reshape(k1, 2, k2)
+    m.A[i + 2] = (s2[:, None] * V2).reshape(k2, 2, chr_)
+    m.c = i + 2
+    m.stats["three_site_updates"] += 1
+    return e1, e2
+
+
 def apply_one(m: MPS, i: int, u: np.ndarray):
     m.A[i] = np.einsum('st,atb->asb', u, m.A[i])
 
@@ -215,7 +263,8 @@ class GateCache:
 
 
 def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
-                cutoff: float, floor_rel: float, gap_rel: float = 1e-4, regauge: bool = False):
+                cutoff: float, floor_rel: float, gap_rel: float = 1e-4, regauge: bool = False,
+                three_site: bool = False):
     t = plan.terms[k]
     g = cache.get(k, v)
     if t.pauli == 'Z':
@@ -235,6 +284,9 @@ def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
         apply_two(m, lo, g, chi_max, cutoff, floor_rel, gap_rel=gap_rel, regauge=regauge)
         return
     assert hi - lo == 2
+    if three_site:
+        apply_three(m, lo, g, chi_max, cutoff, floor_rel, gap_rel=gap_rel)
+        return
     # bring the site at hi next to lo, apply the gate, move it back
     apply_two(m, lo + 1, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel,
               regauge=regauge)
@@ -294,7 +346,7 @@ def expect_string(m: MPS, codes) -> float:
 
 def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
                floor_rel: float = 1e-14, gap_rel: float = 1e-4, regauge: bool = False,
-               strings=None) -> np.ndarray:
+               strings=None, three_site: bool = False) -> np.ndarray:
     cache = GateCache(plan)
     out = []
     e = 0
@@ -302,7 +354,7 @@ def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
     for js in snap_steps:
         while e < ne and events[e, 0] <= js:
             apply_event(m, plan, cache, int(events[e, 1]), int(events[e, 2]),
-                        chi_max, cutoff, floor_rel, gap_rel, regauge)
+                        chi_max, cutoff, floor_rel, gap_rel, regauge, three_site)
             e += 1
         out.append(expect_z(m) if strings is None else np.array([expect_string(m, r) for r in strings]))
     return np.array(out)

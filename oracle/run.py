@@ -18,7 +18,7 @@ from . import statevector as sv
 
 def run(prob, par, init_tensors=None, use_statevector: bool = False,
         floor_rel: float = 1e-14, gap_rel: float = 1e-4, samples=None,
-        regauge: bool = False):
+        regauge: bool = False, three_site: bool = False):
     """Return dict with v (Ns, M, n_obs), sign (Ns, M), gnorm (M,), mean,
     stderr, partials, events_total, per-sample MPS statistics and each
     sample's final MPS (site tensors in chain order; MPS runs only)."""
@@ -51,7 +51,7 @@ def run(prob, par, init_tensors=None, use_statevector: bool = False,
             m = (mps_mod.product_state(prob.init_bits, prob.periodic) if init_tensors is None
                  else mps_mod.canonicalize(init_tensors, prob.periodic))
             z = mps_mod.run_events(m, plan, ev, snaps, par.chi_max, par.cutoff, floor_rel, gap_rel,
-                                   regauge, strings)
+                                   regauge, strings, three_site)
             stats.append(m.stats)
             states.append([a.copy() for a in m.A])
         vs.append(z[:, obs])

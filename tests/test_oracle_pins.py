@@ -486,3 +486,58 @@ def test_continuous_mps_equals_statevector():
     r2 = R.run(prob, par, use_statevector=True)
     assert np.max(np.abs(r1["v"] - r2["v"])) < 1e-12
     assert np.array_equal(r1["sign"], r2["sign"]) and np.all(r1["nu"] > 0)
+
+
+# ---------------------------------------------------------------- P16
+@pytest.mark.parametrize("n", [5, 6, 7])
+def test_three_site_update_untruncated_equals_statevector(n):
+    """Bond-2 gates as one three-site update (no swaps) reproduce the exact
+    circuit when nothing is truncated."""
+    prob = W.spin_ring(n, 1.0, seed=n)
+    par = W.Params(T=1.0, n_steps=60, delta=math.pi / 24, n_samples=3, chi_max=2 ** (n // 2),
+                   cutoff=0.0, n_snapshots=3, seed=5)
+    r1 = R.run(prob, par, three_site=True)
+    r2 = R.run(prob, par, use_statevector=True)
+    assert np.max(np.abs(r1["v"] - r2["v"])) < 1e-12
+    assert all(st["three_site_updates"] > 0 and st["swap_updates"] == 0 for st in r1["stats"])
+
+
+def test_three_site_truncation_fidelity_is_the_product_of_kept_weights():
+    """Truncating the first split projects onto the kept left Schmidt vectors
+    (kept weight 1 - e1); the second split's kept subspace lies inside that
+    range, so the truncated state has fidelity exactly (1 - e1)(1 - e2) with
+    the exact gated state. Checked against a dense contraction."""
+    rng = np.random.default_rng(4)
+    ts, _ = W.random_mps_tensors(8, 8, seed=11)
+    m = M.canonicalize(ts)
+    psi = _dense_from_tensors(m.A)
+    psi = psi / np.linalg.norm(psi)
+    g, _ = np.linalg.qr(rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4)))
+    # dense gate on sites 2 and 4 of the open chain (basis |s_2 s_4>)
+    ex = np.einsum('xysu,abscudef->abxcydef', g.reshape(2, 2, 2, 2), psi.reshape([2] * 8)).reshape(-1)
+    e1, e2 = M.apply_three(m, 2, g, chi_max=5, cutoff=0.0, floor_rel=1e-14)
+    assert e1 > 1e-4 and e2 > 1e-4
+    got = _dense_from_tensors(m.A)
+    assert abs(np.linalg.norm(got) - 1.0) < 1e-12
+    fid = abs(np.vdot(ex, got)) ** 2
+    assert abs(fid - (1 - e1) * (1 - e2)) < 1e-12
+    # left-orthonormal sites 2 and 3, centre on 4
+    for p in (2, 3):
+        a = m.A[p].reshape(-1, m.A[p].shape[2])
+        assert np.allclose(a.conj().T @ a, np.eye(a.shape[1]), atol=1e-12)
+    assert m.c == 4
+
+
+def test_three_site_truncates_less_than_swap_routing():
+    """On a truncated ring (12 sites, chi = 8) the three-site update, which
+    truncates twice per bond-2 gate instead of three times, stays closer to the
+    exact circuit in every sample."""
+    prob = W.spin_ring(12, 1.0, seed=5)
+    par = W.Params(T=1.0, n_steps=100, delta=math.pi / 16, n_samples=6, chi_max=8, cutoff=0.0,
+                   n_snapshots=4, seed=2)
+    a = R.run(prob, par)
+    b = R.run(prob, par, three_site=True)
+    c = R.run(prob, par, use_statevector=True)
+    ea = np.mean(np.abs(a["v"] - c["v"]), axis=(1, 2))
+    eb = np.mean(np.abs(b["v"] - c["v"]), axis=(1, 2))
+    assert np.all(eb < ea) and np.mean(eb) < 0.7 * np.mean(ea)
