@@ -505,7 +505,7 @@ __device__ __forceinline__ int clock_argmin(const double* tn, int L, double* red
   return bk;
 }
 
-__device__ inline SmemLayout carve_smem(unsigned char* base, const KArgs& a, int csize) {
+__host__ __device__ inline SmemLayout carve_smem(unsigned char* base, const KArgs& a, int csize) {
   SmemLayout s;
   size_t o = 0;
   s.dims = reinterpret_cast<int*>(base + o); o += align_up((size_t)(a.n + 1) * 4, 16);
