@@ -541,3 +541,74 @@ def test_three_site_truncates_less_than_swap_routing():
     ea = np.mean(np.abs(a["v"] - c["v"]), axis=(1, 2))
     eb = np.mean(np.abs(b["v"] - c["v"]), axis=(1, 2))
     assert np.all(eb < ea) and np.mean(eb) < 0.7 * np.mean(ea)
+
+
+# ---------------------------------------------------------------- P4b
+def test_finite_n_gaps_are_geometric():
+    """Independent per-gate draws: the steps between successive events of one
+    term follow Geometric(q_k) (chi-squared test over gap bins); a counter
+    or key mix-up that correlated draws across steps would fail it."""
+    import scipy.stats as st
+    prob = W.spin_ring(4, 1.0, seed=2)
+    T, N, delta = 1.0, 40, math.pi / 16
+    plan = planner.make_plan(prob, T, N, delta)
+    k = int(np.argmax(plan.q))
+    q = float(plan.q[k])
+    assert 0.2 < q < 0.8
+    # from each start point (step 0 or an event of term k) with at least 6
+    # steps left, the next event of term k comes 1..6 steps later or not
+    # within 6 steps: fully observed categories, i.i.d. Geometric(q) by the
+    # independence of the draws
+    obs = np.zeros(7)
+    for s in range(1500):
+        ev = sampler.sample_events(plan, 3, s, N)
+        j = ev[ev[:, 1] == k, 0]
+        for j0 in np.concatenate([[0], j]):
+            if j0 > N - 6:
+                break
+            nxt = j[j > j0]
+            g = int(nxt[0] - j0) if len(nxt) else N + 1
+            obs[min(g, 7) - 1] += 1
+    p = np.array([q * (1 - q) ** (g - 1) for g in range(1, 7)] + [(1 - q) ** 6])
+    exp = p * obs.sum()
+    chi2 = float(np.sum((obs - exp) ** 2 / exp))
+    assert st.chi2.sf(chi2, len(obs) - 1) > 1e-3, (obs, exp)
+
+
+def test_continuous_gaps_are_exponential():
+    """Waiting times between successive events of one term in the N -> infinity
+    sampler are Exp(lam_k) (Kolmogorov-Smirnov), and C marks are independent of
+    the gaps (equal mean gap before B and C events within the statistics)."""
+    import scipy.stats as st
+    prob = W.spin_ring(4, 1.0, seed=2)
+    par = W.Params(T=1.0, n_steps=100, delta=math.pi / 4, n_samples=1, chi_max=4, cutoff=0.0,
+                   n_snapshots=2, variant=planner.CONTINUOUS)
+    plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, planner.CONTINUOUS)
+    ts = planner.snapshot_times(plan, par.steps_run(), par.n_snapshots)
+    k = int(np.argmax(plan.lam))
+    lam = float(plan.lam[k])
+    # from each start point (t = 0 or an event of term k) at least `cut` before
+    # t_M, the wait to the next event of term k is observed if it is < cut:
+    # such waits follow Exp(lam) conditioned on < cut
+    cut = ts[-1] / 2
+    g, gaps, marks = [], [], []
+    for s in range(1500):
+        ev, tt = sampler.sample_events_continuous(plan, 5, s, ts)
+        sel = ev[:, 1] == k
+        t = tt[sel]
+        gaps.extend(np.diff(np.concatenate([[0.0], t])).tolist())
+        marks.extend(ev[sel, 2].tolist())
+        for t0 in np.concatenate([[0.0], t]):
+            if t0 > ts[-1] - cut:
+                break
+            nxt = t[t > t0]
+            if len(nxt) and nxt[0] - t0 < cut:
+                g.append(nxt[0] - t0)
+    gaps = np.array(gaps)
+    marks = np.array(marks)
+    cdf = lambda x: (1 - np.exp(-lam * x)) / (1 - math.exp(-lam * cut))
+    assert len(g) > 1000 and st.kstest(np.array(g), cdf).pvalue > 1e-3
+    c = marks == sampler.EV_C
+    assert c.sum() > 100
+    d = gaps[c].mean() - gaps[~c].mean()
+    assert abs(d) < 4 * gaps.std() * math.sqrt(1 / c.sum() + 1 / (~c).sum())
