@@ -51,7 +51,7 @@ def parse():
                          "samples straggle, stays below 10%% of a step)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-tts", action="store_true", help="skip the config-1 time-to-<Z> comparison")
+    ap.add_argument("--no-tts", action="store_true", help="skip the ring-of-8 time-to-<Z> comparison")
     ap.add_argument("--n", type=int, default=64, help="ring size (profiling cases only)")
     ap.add_argument("--chi", type=int, default=128, help="bond cap (profiling cases only)")
     return ap.parse_args()
@@ -168,14 +168,14 @@ def run_reference(a):
     return 0
 
 
-# ---------------------------------------------------------------- time to <Z>, config 1
-def tts_config1(T, W, torch, local, subset=16):
-    """Time-to-<Z_0> on configuration 1 (ring of 8, 1000 samples, N = 2000):
+# ---------------------------------------------------------------- time to <Z>, ring of 8
+def tts_ring8(T, W, torch, local, subset=16):
+    """Time-to-<Z_0> on the ring8_heisenberg_T1 workload (ring of 8, 1000 samples, N = 2000):
     mixed precision with batched persistent CTAs, against the plain FP64 form
     with one sample per launch (timed on `subset` samples, scaled to 1000).
     The error is max |mean_mixed - mean_fp64| on the same seeded circuits. The
     FP64 path equals the oracle to 1e-10 in the parity tests."""
-    prob, par, _ = W.config(1)
+    prob, par, _ = W.workload(W.RING8)
     ctx = T.tepai_create(local)
     try:
         mixed = W.Params(**{**par.__dict__, "precision": 1})
@@ -356,7 +356,7 @@ def run_ours(a):
                   "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi, "grid_ctas": grid},
     }
     if not a.no_tts and world == 1:
-        line["tts_config1"] = tts_config1(T, W, torch, local)
+        line["tts_ring8"] = tts_ring8(T, W, torch, local)
     if not a.no_cpu_baseline and world == 1:
         procs = max(1, min(cpu_cores(), 16))
         u, t = oracle_sample(1, [base + 900_000 + i for i in range(procs)], procs)

@@ -34,9 +34,9 @@ def test_library_exports_every_declared_symbol(T):
     assert set(T.EXPORTED) == set(names)
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("cfg", [W.RING8, W.RING32, W.RING64_XXZ, W.RING100, W.RING64_HYBRID])
 def test_host_planner_matches_oracle(T, cfg):
-    prob, par, _ = W.config(cfg)
+    prob, par, _ = W.workload(cfg)
     g, nu = T.tepai_gnorm(prob, par)
     plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, par.variant)
     snaps = planner.snapshot_steps(par.n_steps, par.n_snapshots)
@@ -46,7 +46,7 @@ def test_host_planner_matches_oracle(T, cfg):
 
 
 def test_invalid_arguments_are_rejected(T):
-    prob, par, _ = W.config(1)
+    prob, par, _ = W.workload(W.RING8)
     bad = W.Params(**{**par.__dict__, "n_steps": 100})      # theta = 0.02 > Delta = pi/256
     with pytest.raises(T.TepaiError) as e:
         T.tepai_gnorm(prob, bad)
@@ -71,18 +71,18 @@ def test_invalid_arguments_are_rejected(T):
 
 
 def test_no_pi_gnorm_is_one(T):
-    prob, par, _ = W.config(2)
+    prob, par, _ = W.workload(W.RING32)
     g, _ = T.tepai_gnorm(prob, W.Params(**{**par.__dict__, "variant": 1}))
     assert np.all(np.abs(g - 1.0) < 1e-15)
 
 
-@pytest.mark.parametrize("cfg", [1, 2])
+@pytest.mark.parametrize("cfg", [W.RING8, W.RING32])
 def test_continuous_host_planner_matches_oracle(T, cfg):
     """N -> infinity sampler: ||g(t_m)||_1 and E[nu] from the host planner equal
     the oracle's to rounding (the oracle sums ||c||_1 with Python's compensated
     sum, the planner plainly); small Delta is no obstacle (no theta <= Delta
     bound), Delta >= pi and runaway event counts are refused."""
-    prob, par, _ = W.config(cfg)
+    prob, par, _ = W.workload(cfg)
     cp = W.Params(**{**par.__dict__, "n_steps": 10, "n_snapshots": 5, "variant": 3})
     g, nu = T.tepai_gnorm(prob, cp)
     plan = planner.make_plan(prob, cp.T, cp.n_steps, cp.delta, planner.CONTINUOUS)

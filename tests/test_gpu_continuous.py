@@ -51,11 +51,11 @@ def _compare(T, ctx, prob, par, tol, use_sv=False):
     return got, ref
 
 
-@pytest.mark.parametrize("cfg", [1, 2])
+@pytest.mark.parametrize("cfg", [W.RING8, W.RING32])
 def test_device_continuous_sampler_matches_oracle(T, ctx, cfg):
     """Bench-sized problems (n = 16 and 32 rings at their Delta): every event's
     snapshot index, term and setting, in time order."""
-    prob, par, _ = W.config(cfg)
+    prob, par, _ = W.workload(cfg)
     par = W.Params(**{**par.__dict__, "variant": CONT, "n_steps": 10, "n_snapshots": 5})
     plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, CONT)
     ts = planner.snapshot_times(plan, par.steps_run(), par.n_snapshots)

@@ -39,9 +39,9 @@ def P(**kw):
 
 
 # ------------------------------------------------------------------ sampler
-@pytest.mark.parametrize("cfg,variant", [(1, 0), (2, 0), (3, 0), (2, 1)])
+@pytest.mark.parametrize("cfg,variant", [(W.RING8, 0), (W.RING32, 0), (W.RING64_XXZ, 0), (W.RING32, 1)])
 def test_device_sampler_matches_oracle(T, ctx, cfg, variant):
-    prob, par, _ = W.config(cfg)
+    prob, par, _ = W.workload(cfg)
     par = W.Params(**{**par.__dict__, "variant": variant})
     plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, variant)
     for s in (0, 1, 12345):
@@ -70,16 +70,16 @@ def test_fp64_untruncated_matches_oracle_mps_and_statevector(T, ctx):
     _compare(T, ctx, prob, par, TOL64, use_sv=True)
 
 
-def test_fp64_trotter_mode_config1_matches_statevector(T, ctx):
-    prob, par, ex = W.config(1)
+def test_fp64_trotter_mode_ring8_matches_statevector(T, ctx):
+    prob, par, ex = W.workload(W.RING8)
     par = W.Params(**{**par.__dict__, "n_steps": ex["trotter_steps"], "variant": 2, "n_samples": 1,
                       "obs_sites": None})
     got, ref, _ = _compare(T, ctx, prob, par, TOL64, use_sv=True)
     assert np.max(np.abs(got["v"].sum(axis=2))) < 1e-10       # sum_i <Z_i> conserved
 
 
-def test_fp64_config1_samples_match_statevector(T, ctx):
-    prob, par, _ = W.config(1)
+def test_fp64_ring8_samples_match_statevector(T, ctx):
+    prob, par, _ = W.workload(W.RING8)
     par = W.Params(**{**par.__dict__, "n_samples": 3, "obs_sites": None})
     _compare(T, ctx, prob, par, TOL64, use_sv=True)
 
@@ -212,8 +212,8 @@ def test_mixed_weakly_truncated_matches_oracle(T, ctx):
     _compare(T, ctx, prob, par, TOLMIX)
 
 
-def test_mixed_config1_matches_statevector(T, ctx):
-    prob, par, _ = W.config(1)
+def test_mixed_ring8_matches_statevector(T, ctx):
+    prob, par, _ = W.workload(W.RING8)
     par = W.Params(**{**par.__dict__, "n_samples": 2, "precision": 1, "obs_sites": None})
     _compare(T, ctx, prob, par, TOLMIX, use_sv=True)
 

@@ -145,7 +145,7 @@ def test_mean_gate_count_and_setting_frequencies():
 
 
 def test_expected_gate_count_tends_to_nu_inf():
-    prob, par, _ = W.config(2)
+    prob, par, _ = W.workload(W.RING32)
     prev = None
     for N in (2000, 8000, 32000):
         plan = planner.make_plan(prob, par.T, N, par.delta)
@@ -159,7 +159,7 @@ def test_expected_gate_count_tends_to_nu_inf():
 
 # ---------------------------------------------------------------- P5
 def test_gnorm_tends_to_limit():
-    prob, par, _ = W.config(1)
+    prob, par, _ = W.workload(W.RING8)
     lim = planner.gnorm_infinity(prob, par.T, par.delta)
     rels = []
     for N in (2000, 20000, 200000):
@@ -415,7 +415,7 @@ def test_continuous_rates_are_the_finite_n_limit():
     """The N -> infinity sampler's rates are the limits of the finite-N draw
     probabilities built from Eq. gammas: q_k N / T -> lam_k, r_k -> r_inf,
     ||g||_1 -> exp(2 tan(Delta/2) ||c||_1 T)."""
-    prob, par, _ = W.config(1)
+    prob, par, _ = W.workload(W.RING8)
     cp = planner.make_plan(prob, par.T, par.n_steps, par.delta, planner.CONTINUOUS)
     errs = []
     for N in (10 ** 4, 10 ** 5, 10 ** 6):

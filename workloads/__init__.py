@@ -105,7 +105,7 @@ def random_mps_tensors(n: int, chi: int, seed: int, dtype=np.complex128):
 
 
 # --------------------------------------------------------------------------
-# The five benchmark configurations of the workload (all synthetic).
+# The paper-scale workloads (all synthetic), by name.
 # N for TE-PAI follows the deep-Trotter baseline N(T) = N_dT (T/dT)^2 with
 # dT = 0.1 and N_dT = 20 (Sec. II.D, Eq. trotter-baseline-scaling).
 # --------------------------------------------------------------------------
@@ -114,44 +114,56 @@ def trotter_baseline_steps(T: float, dT: float = 0.1, N_dT: int = 20) -> int:
     return int(round(N_dT * (T / dT) ** 2))
 
 
-def config(idx: int) -> tuple[Problem, Params, dict]:
-    """Return (problem, params, extra) for configuration idx in 1..5."""
-    if idx == 1:
+RING8 = "ring8_heisenberg_T1"
+RING32 = "ring32_heisenberg_T2"
+RING64_XXZ = "ring64_xxz_T3"
+RING100 = "ring100_heisenberg_T4"
+RING64_HYBRID = "ring64_hybrid_T2to5"
+
+
+def workload(name: str) -> tuple[Problem, Params, dict]:
+    """Return (problem, params, extra) of a named workload:
+    ring8_heisenberg_T1    n = 8 Heisenberg ring, T = 1, chi 16, 1000 samples, <Z_0>;
+    ring32_heisenberg_T2   n = 32, fields U[-2, 2], T = 2, chi 64, 10^4 samples;
+    ring64_xxz_T3          n = 64 XXZ (Jz = 0.5), T = 3, chi 128, 10^5 samples;
+    ring100_heisenberg_T4  n = 100, fields U[-3, 3], T = 4, chi 32 (and 256);
+    ring64_hybrid_T2to5    n = 64, chi 256, TE-PAI on [2, 5] after a Trotter prefix."""
+    if name == RING8:
         prob = spin_ring(8, 1.0, seed=0)
         par = Params(T=1.0, n_steps=trotter_baseline_steps(1.0), delta=math.pi / 256,
                      n_samples=1000, chi_max=16, cutoff=0.0, n_snapshots=10,
                      seed=0, precision=0, obs_sites=np.array([0], dtype=np.int32))
         return prob, par, {"trotter_steps": 100, "name": "ring8_heisenberg_T1"}
-    if idx == 2:
+    if name == RING32:
         prob = spin_ring(32, 2.0, seed=0)
         par = Params(T=2.0, n_steps=trotter_baseline_steps(2.0), delta=math.pi / 512,
                      n_samples=10_000, chi_max=64, cutoff=1e-10, n_snapshots=20,
                      seed=0, precision=1)
         return prob, par, {"name": "ring32_heisenberg_T2"}
-    if idx == 3:
+    if name == RING64_XXZ:
         prob = spin_ring(64, 1.0, seed=0, Jz=0.5)
         par = Params(T=3.0, n_steps=trotter_baseline_steps(3.0), delta=math.pi / 1024,
                      n_samples=100_000, chi_max=128, cutoff=1e-10, n_snapshots=1,
                      seed=0, precision=1)
         return prob, par, {"name": "ring64_xxz_T3"}
-    if idx == 4:
+    if name == RING100:
         prob = spin_ring(100, 3.0, seed=0)
         par = Params(T=4.0, n_steps=trotter_baseline_steps(4.0), delta=math.pi / 1024,
                      n_samples=50_000, chi_max=32, cutoff=1e-10, n_snapshots=1,
                      seed=0, precision=1)
         return prob, par, {"name": "ring100_heisenberg_T4", "chi_alt": 256}
-    if idx == 5:
+    if name == RING64_HYBRID:
         prob = spin_ring(64, 1.0, seed=0)
         par = Params(T=3.0, n_steps=trotter_baseline_steps(3.0), delta=math.pi / 1024,
                      n_samples=20_000, chi_max=256, cutoff=1e-10, n_snapshots=1,
                      seed=0, precision=1)
         return prob, par, {"name": "ring64_hybrid_T2to5", "t0": 2.0}
-    raise ValueError(idx)
+    raise ValueError(name)
 
 
 # --------------------------------------------------------------------------
 # Benchmark workload: steady state at chi = 128.
-# Configuration 3's ring (n = 64 XXZ, Jz = 0.5, h ~ U[-1, 1], T = 3,
+# The ring64_xxz_T3 ring (n = 64 XXZ, Jz = 0.5, h ~ U[-1, 1], T = 3,
 # Delta = pi/1024, N = 18000, chi_max = 128, cutoff 1e-10). Every sample starts
 # from one shared random MPS whose bonds are already at the cap, so that every
 # two-site update runs at chi = 128. Each sample then evolves a window of the
@@ -161,7 +173,7 @@ def config(idx: int) -> tuple[Problem, Params, dict]:
 
 def bench_workload(n_samples: int, window_steps: int = 2, sample_offset: int = 0,
                    chi: int = 128, mps_seed: int = 1234, n: int = 64):
-    prob, par, extra = config(3)
+    prob, par, extra = workload(RING64_XXZ)
     if n != prob.n:
         prob = spin_ring(n, 1.0, seed=0, Jz=0.5)
     par = Params(T=par.T, n_steps=par.n_steps, delta=par.delta, n_samples=n_samples,
