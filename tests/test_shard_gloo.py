@@ -60,3 +60,44 @@ def test_gloo_two_ranks_merge_equals_single_process(tmp_path):
         got = np.load(tmp_path / f"r{r}.npy")
         assert np.allclose(got[0], mean, rtol=0, atol=1e-15)
         assert np.allclose(got[1], se, rtol=1e-12, atol=1e-15)
+
+
+def _oracle_worker(rank, world, port, out_dir):
+    """Each rank runs the oracle on its own range of global sample indices of
+    the N -> infinity sampler and the ranks merge their partials."""
+    import math
+    import torch.distributed as dist
+    import workloads as W
+    from oracle import run as orun
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    prob = W.spin_ring(4, 1.0, seed=1)
+    ns = 9
+    off, cnt = shard.shard_range(ns, rank, world, offset=100)
+    par = W.Params(T=0.5, n_steps=10, delta=math.pi / 8, n_samples=cnt, chi_max=4, cutoff=0.0,
+                   n_snapshots=2, seed=4, sample_offset=off, variant=3)
+    r = orun.run(prob, par, use_statevector=True)
+    mean, se = shard.allgather_merge(r["partials"], cnt, r["gnorm"], dist)
+    np.save(os.path.join(out_dir, f"c{rank}.npy"), np.stack([mean, se]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_sharded_continuous_sampler_equals_single_process(tmp_path):
+    """Circuits are keyed by the global sample index, so two ranks running
+    disjoint index ranges reproduce the single-process N -> infinity estimate."""
+    import math
+    import workloads as W
+    from oracle import run as orun
+    torch_mp = pytest.importorskip("torch.multiprocessing")
+    port = _free_port()
+    torch_mp.spawn(_oracle_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    prob = W.spin_ring(4, 1.0, seed=1)
+    par = W.Params(T=0.5, n_steps=10, delta=math.pi / 8, n_samples=9, chi_max=4, cutoff=0.0,
+                   n_snapshots=2, seed=4, sample_offset=100, variant=3)
+    ref = orun.run(prob, par, use_statevector=True)
+    for r in range(2):
+        got = np.load(tmp_path / f"c{r}.npy")
+        assert np.allclose(got[0], ref["mean"], rtol=0, atol=1e-14)
+        assert np.allclose(got[1], ref["stderr"], rtol=1e-12, atol=1e-14)
