@@ -432,8 +432,10 @@ def test_continuous_rates_are_the_finite_n_limit():
 
 def test_continuous_sampler_counts_and_times():
     """Poisson law of the continuous sampler: per term, E[count] = lam_k t_M with
-    variance equal to the mean; the C fraction is r_inf; given the count, the
-    event times are uniform on [0, t_M] (mean t_M / 2)."""
+    variance equal to the mean, so the total gate count has mean nu_inf and
+    standard deviation sqrt(nu_inf), the limit law App. A.5 states; the C
+    fraction is r_inf; given the count, the event times are uniform on
+    [0, t_M] (mean t_M / 2)."""
     prob = W.spin_ring(4, 1.0, seed=2)
     par = W.Params(T=1.0, n_steps=100, delta=math.pi / 8, n_samples=1, chi_max=4, cutoff=0.0,
                    n_snapshots=4, variant=planner.CONTINUOUS)
