@@ -18,12 +18,14 @@ in the natural order.
     k_cut   = the smallest k with sum_{j>=k} s_j^2 <= cutoff * sum_j s_j^2;
     k_floor = #{j : s_j > floor_rel * s_0}, which drops singular values that
               are zero to working precision.
-  A cut never splits a group of (nearly) equal singular values: when
-  s_{k-1} - s_k <= gap_rel * s_0 (default 1e-4), k drops to the largest k' < k
-  with a clear gap there (the whole tied group is discarded). This makes the
-  truncated state unique, and it bounds how far a rounding-level change of
-  theta can move the kept subspace (by about s_k * rounding / gap). If no such
-  k' >= 1 exists, k stays as it is.
+  A cut never splits a group of singular values that are equal to working
+  precision: when s_{k-1} - s_k <= gap_rel * s_0, k drops to the largest
+  k' < k with a gap there (the whole tied group is discarded); if no such
+  k' >= 1 exists, k stays as it is. The paper keeps "the chi largest"
+  singular values and says nothing of ties; the default gap_rel = 1e-12
+  (PAPER_TIE_REL) only settles exactly degenerate groups, whose kept state
+  the paper's rule leaves undefined. A wider band (e.g. 1e-4) is an explicit
+  option, taken by both this oracle and the CUDA path when set.
 - A single-site gate, and a pi-rotation of a bond term (a product of two
   single-site Paulis), act on the physical index directly. A unitary on one
   site keeps every canonical condition.
@@ -49,6 +51,10 @@ from . import gates
 from .sampler import EV_B, EV_C, EV_T
 
 ZDIAG = np.array([1.0, -1.0])
+
+# Tie band of the paper's truncation rule: only groups of singular values equal
+# to working precision (relative gaps <= 1e-12) count as ties at a cut.
+PAPER_TIE_REL = 1e-12
 
 
 def chain_order(n: int, periodic: bool) -> list:
@@ -138,7 +144,7 @@ def canonicalize(tensors, periodic: bool = False) -> MPS:
 
 
 def keep_count(s: np.ndarray, chi_max: int, cutoff: float, floor_rel: float,
-               gap_rel: float = 0.0) -> int:
+               gap_rel: float = PAPER_TIE_REL) -> int:
     if s.size == 0 or s[0] <= 0.0:
         return 1
     w = s.astype(np.float64) ** 2
@@ -166,7 +172,7 @@ def keep_count(s: np.ndarray, chi_max: int, cutoff: float, floor_rel: float,
 
 
 def apply_two(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float,
-              floor_rel: float, swap: bool = False, gap_rel: float = 1e-4,
+              floor_rel: float, swap: bool = False, gap_rel: float = PAPER_TIE_REL,
               regauge: bool = False):
     """Two-site update on bond (i, i+1) with a 4x4 gate g (basis |s_i s_{i+1}>).
     regauge=True moves the centre back to site i afterwards: an exact change of
@@ -216,7 +222,7 @@ def _split(m: MPS, M: np.ndarray, chi_max: int, cutoff: float, floor_rel: float,
 
 
 def apply_three(m: MPS, i: int, g: np.ndarray, chi_max: int, cutoff: float, floor_rel: float,
-                gap_rel: float = 1e-4):
+                gap_rel: float = PAPER_TIE_REL):
     """Gate g (4x4, basis |s_i s_{i+2}>) on chain positions i and i+2 as one
     three-site update (see the module notes); the centre ends on i+2.
     Returns the discarded weight fractions of the two splits."""
@@ -263,7 +269,7 @@ class GateCache:
 
 
 def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
-                cutoff: float, floor_rel: float, gap_rel: float = 1e-4, regauge: bool = False,
+                cutoff: float, floor_rel: float, gap_rel: float = PAPER_TIE_REL, regauge: bool = False,
                 three_site: bool = False):
     t = plan.terms[k]
     g = cache.get(k, v)
@@ -345,7 +351,7 @@ def expect_string(m: MPS, codes) -> float:
 
 
 def run_events(m: MPS, plan, events, snap_steps, chi_max: int, cutoff: float,
-               floor_rel: float = 1e-14, gap_rel: float = 1e-4, regauge: bool = False,
+               floor_rel: float = 1e-14, gap_rel: float = PAPER_TIE_REL, regauge: bool = False,
                strings=None, three_site: bool = False) -> np.ndarray:
     cache = GateCache(plan)
     out = []

@@ -17,7 +17,7 @@ from . import statevector as sv
 
 
 def run(prob, par, init_tensors=None, use_statevector: bool = False,
-        floor_rel: float = 1e-14, gap_rel: float = 1e-4, samples=None,
+        floor_rel: float = 1e-14, gap_rel: float = mps_mod.PAPER_TIE_REL, samples=None,
         regauge: bool = False, three_site: bool = False):
     """Return dict with v (Ns, M, n_obs), sign (Ns, M), gnorm (M,), mean,
     stderr, partials, events_total, per-sample MPS statistics and each

@@ -267,22 +267,64 @@ def test_estimate_matches_plain_mean_and_std():
 
 
 # ---------------------------------------------------------------- truncation / MPS
-def test_keep_count_brute_force():
+def _keep_brute(s, chi, cut, floor_rel, gap_rel):
+    """The keep rule by exhaustive search over cut positions: the target is the
+    largest kk that is at most chi, at most the number of values above the
+    floor, and at most the first kk whose discarded tail is within the cutoff.
+    When the value right after the target is above the floor, the cut must sit
+    at a clear gap (s_{kk-1} - s_kk > gap_rel s_0): the largest such kk at or
+    below the target wins, and without one the target stays."""
+    n = len(s)
+    tot = float(np.sum(s ** 2))
+    tails = [float(np.sum(s[kk:] ** 2)) for kk in range(n + 1)]
+    k_cut = next(kk for kk in range(1, n + 1) if tails[kk] <= cut * tot or kk == n)
+    above = [j for j in range(n) if s[j] > floor_rel * s[0]]
+    target = max(1, min([chi, len(above), k_cut, n]))
+    if target == n or not (s[target] > floor_rel * s[0]):
+        return target
+    clear = [kk for kk in range(1, target + 1) if s[kk - 1] - s[kk] > gap_rel * s[0]]
+    return max(clear) if clear else target
+
+
+@pytest.mark.parametrize("floor_rel,gap_rel", [(1e-14, 1e-12), (1e-14, 1e-4), (4e-6, 1e-4), (4e-6, 1e-12)])
+def test_keep_count_brute_force(floor_rel, gap_rel):
+    """keep_count against the brute-force rule, with planted exact ties, near
+    ties inside and outside the band (gaps of 0.5 and 2 band widths measured
+    against s_0, so a band taken relative to s_k instead of s_0 fails), and
+    values planted just below and above the floor."""
     rng = np.random.default_rng(2)
-    for _ in range(400):
-        s = np.sort(rng.exponential(1.0, rng.integers(1, 12)) ** 3)[::-1]
-        if len(s) > 2 and rng.random() < 0.5:          # plant a tied group
+    planted = {"tie": 0, "in": 0, "out": 0, "floor": 0}
+    for _ in range(1500):
+        s = np.sort(rng.exponential(1.0, rng.integers(1, 14)) ** 3)[::-1]
+        if len(s) > 2:
             i = int(rng.integers(1, len(s) - 1))
-            s[i + 1] = s[i]
-        chi, cut = int(rng.integers(1, 10)), float(10.0 ** rng.uniform(-6, -0.5))
-        k = M.keep_count(s, chi, cut, 1e-14, gap_rel=1e-12)
-        tot = np.sum(s ** 2)
-        ok = [kk for kk in range(1, len(s) + 1) if np.sum(s[kk:] ** 2) <= cut * tot]
-        k0 = max(1, min(chi, ok[0], len(s)))
-        # cuts allowed: the end, or a place with a strict gap; take the largest <= k0
-        allowed = [kk for kk in range(1, k0 + 1) if kk == len(s) or s[kk - 1] > s[kk]]
-        assert k == (max(allowed) if allowed else k0)
-        assert k == len(s) or s[k - 1] > s[k] or not allowed
+            kind = rng.choice(["tie", "in", "out", "floor", "none"])
+            if kind == "tie":
+                s[i + 1] = s[i]
+            elif kind == "in":
+                s[i + 1] = max(s[i] - 0.5 * gap_rel * s[0], 0.0)
+            elif kind == "out":
+                s[i + 1] = max(s[i] - 2.0 * gap_rel * s[0], 0.0)
+            elif kind == "floor":
+                s[i] = (0.5 if rng.random() < 0.5 else 2.0) * floor_rel * s[0]
+                s[i + 1:] = np.minimum(s[i + 1:], s[i])
+            s = np.sort(s)[::-1]
+            if kind in planted:
+                planted[kind] += 1
+        chi, cut = int(rng.integers(1, 12)), float(10.0 ** rng.uniform(-14, -0.5))
+        k = M.keep_count(s, chi, cut, floor_rel, gap_rel=gap_rel)
+        assert k == _keep_brute(s, chi, cut, floor_rel, gap_rel), (s, chi, cut, k)
+    assert min(planted.values()) > 100
+
+
+def test_keep_count_default_is_the_paper_rule():
+    """Default band: only equal values are held together; a gap of 1e-9 s_0
+    (far above FP64 rounding) is a valid cut, and an exact tie is not."""
+    s = np.array([1.0, 0.5, 0.5 - 1e-9, 0.2])
+    assert M.keep_count(s, 2, 0.0, 1e-14) == 2
+    s = np.array([1.0, 0.5, 0.5, 0.2])
+    assert M.keep_count(s, 2, 0.0, 1e-14) == 1
+    assert M.PAPER_TIE_REL == 1e-12
 
 
 def test_truncated_update_discards_weight_per_eckart_young():
