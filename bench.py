@@ -29,13 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TE-PAI MPS gate-updates/s at chi=128"
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one ensemble_kernel
-# launch of the default workload, divided by the two-site updates of that launch
-# (7.897e12 B over 123751 updates), from one ncu capture of the current kernel.
-DRAM_BYTES_PER_UPDATE = 6.381e7
 UNIT = "updates/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
 
@@ -54,6 +48,12 @@ def parse():
     ap.add_argument("--no-tts", action="store_true", help="skip the ring-of-8 time-to-<Z> comparison")
     ap.add_argument("--n", type=int, default=64, help="ring size (profiling cases only)")
     ap.add_argument("--chi", type=int, default=128, help="bond cap (profiling cases only)")
+    ap.add_argument("--tts-ring32", type=int, default=0, metavar="K",
+                    help="also time K full ring32_heisenberg_T2 circuits (chi 64, mixed) and report the "
+                         "time-to-<Z> of its 10^4 samples, extrapolated from the K timed ones")
+    ap.add_argument("--launch-variant", type=int, default=0,
+                    help="tepai_params.launch_variant (0 = library default; 2 = CUDA-core Jacobi, "
+                         "7 = tensor-core Jacobi), for A/B runs")
     return ap.parse_args()
 
 
@@ -105,29 +105,35 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- oracle leg
 def _oracle_worker(args):
+    """One bench sample through the FP64 oracle, as it stands. The sample's
+    set-up (interpreter start, imports, the shared start state's canonical
+    form, the circuit draw) is outside the timed region: only the evolution of
+    the sample's events is timed."""
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     window, offset = args
     import workloads as W
-    from oracle import run as orun
+    from oracle import mps as omps
+    from oracle import planner, sampler
     prob, par, init = W.bench_workload(1, window_steps=window, sample_offset=offset)
+    plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, par.variant)
+    ev = sampler.sample_events(plan, par.seed, offset, par.steps_run())
+    m = omps.canonicalize(init[0], prob.periodic)
     t = time.perf_counter()
-    r = orun.run(prob, par, init_tensors=init[0], floor_rel=4e-6, gap_rel=1e-4)
+    omps.run_events(m, plan, ev, [par.steps_run()], par.chi_max, par.cutoff, floor_rel=4e-6)
     dt = time.perf_counter() - t
-    st = r["stats"][0]
-    return st["gate_updates"] + st["swap_updates"], dt
+    return m.stats["gate_updates"] + m.stats["swap_updates"], dt
 
 
 def oracle_sample(window: int, offsets, procs: int):
-    """The FP64 oracle, as it stands, on `procs` host processes (one BLAS thread
-    each), one bench sample per process. Returns (updates, wall seconds)."""
+    """The FP64 oracle on `procs` host processes (one BLAS thread each), one
+    bench sample per process. Returns (updates, aggregate updates/s): the sum
+    over processes of each one's updates per second of evolution."""
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
     ctx = mp.get_context("spawn")
-    t = time.perf_counter()
     with ctx.Pool(procs) as pool:
         res = pool.map(_oracle_worker, [(window, o) for o in offsets])
-    wall = time.perf_counter() - t
-    return sum(u for u, _ in res), wall
+    return sum(u for u, _ in res), sum(u / t for u, t in res if t > 0)
 
 
 def cpu_cores() -> int:
@@ -142,33 +148,67 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    procs = max(1, min(cpu_cores(), 16))
+    procs = cpu_cores()
     window = 1
     batch = procs
     for w in range(a.warmup):
         oracle_sample(window, [10_000_000 + w * batch + i for i in range(batch)], procs)
-    tot_u, tot_t = 0.0, 0.0
+    rates, t0 = [], time.perf_counter()
     for s in range(a.steps):
-        u, t = oracle_sample(window, [20_000_000 + s * batch + i for i in range(batch)], procs)
-        tot_u += u
-        tot_t += t
-    val = tot_u / tot_t
+        _, r = oracle_sample(window, [20_000_000 + s * batch + i for i in range(batch)], procs)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    val = sum(rates) / len(rates)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_t / a.steps,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * wall / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "ring64_xxz_chi128_window", "n": 64, "chi_max": 128,
                        "window_steps": window, "batch": batch, "init": "shared random MPS at chi=128",
                        "l2": "host CPU run"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": procs, "kind": "oracle",
-                             "sample": f"{batch} samples x {window} Trotter step(s) per step, "
-                                       f"one process (1 BLAS thread) per sample"},
+                             "sample": f"{batch} samples x {window} Trotter step(s) per step, one process "
+                                       f"(1 BLAS thread) per sample on every core of the affinity mask "
+                                       f"(nproc {procs}); evolution timed, set-up not"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ---------------------------------------------------------------- time to <Z>, ring of 8
+def _sv_ring8_chunk(args):
+    """State-vector oracle values of samples [lo, hi) of ring8_heisenberg_T1."""
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    lo, hi = args
+    import workloads as W
+    from oracle import run as orun
+    prob, par, _ = W.workload(W.RING8)
+    r = orun.run(prob, par, use_statevector=True, samples=range(lo, hi))
+    return r["v"], r["sign"]
+
+
+def ring8_oracle_mean():
+    """Exact state-vector oracle estimate of ring8_heisenberg_T1 (all circuits,
+    spawned processes with one BLAS thread each). Returns (mean [M][1], seconds)."""
+    import numpy as np
+    import workloads as W
+    from oracle import estimator, planner
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    prob, par, _ = W.workload(W.RING8)
+    chunks = [(lo, min(lo + 25, par.n_samples)) for lo in range(0, par.n_samples, 25)]
+    t = time.perf_counter()
+    with mp.get_context("spawn").Pool(cpu_cores()) as pool:
+        res = pool.map(_sv_ring8_chunk, chunks)
+    dt = time.perf_counter() - t
+    v = np.concatenate([r[0] for r in res])
+    sg = np.concatenate([r[1] for r in res])
+    plan = planner.make_plan(prob, par.T, par.n_steps, par.delta, par.variant)
+    g = np.array([planner.gnorm_at(plan, j) for j in planner.snapshot_steps(par.n_steps, par.n_snapshots)])
+    mean, _, _ = estimator.estimate(v, sg, g)
+    return mean, dt
+
+
 def tts_ring8(T, W, torch, local, subset=16):
     """Time-to-<Z_0> on the ring8_heisenberg_T1 workload (ring of 8, 1000 samples, N = 2000):
     mixed precision with batched persistent CTAs, against the plain FP64 form
@@ -199,11 +239,16 @@ def tts_ring8(T, W, torch, local, subset=16):
     finally:
         T.tepai_destroy(ctx)
     err = float(abs(rm["mean"] - rf["mean"]).max())
+    ref_mean, t_oracle = ring8_oracle_mean()
     return {"config": "ring8_heisenberg_T1 (N=2000, 1000 samples, chi_max=16, <Z_0> at 10 times)",
             "mixed_batched_s": t_mixed, "fp64_batched_s": t_fp64_batched,
             "fp64_one_sample_per_launch_s": t_one, "one_per_launch_subset": subset,
             "speedup_vs_fp64_one_per_launch": t_one / t_mixed,
             "max_abs_err_mixed_vs_fp64": err,
+            "err_per_snapshot_mixed_vs_oracle": [float(x) for x in abs(rm["mean"] - ref_mean)[:, 0]],
+            "err_per_snapshot_fp64_vs_oracle": [float(x) for x in abs(rf["mean"] - ref_mean)[:, 0]],
+            "oracle": f"exact state vector on all {par.n_samples} circuits, {cpu_cores()} host processes, "
+                      f"{t_oracle:.1f} s",
             "stderr_fp64": float(rf["stderr"].max()),
             "mixed_continuous_s": t_cont,
             "events_per_sample_finite_n": rm["stats"]["events"] / par.n_samples,
@@ -213,6 +258,33 @@ def tts_ring8(T, W, torch, local, subset=16):
             "sampler_phase_share_finite_n": rm["stats"]["phase_cycles"]["sampler"]
             / max(1.0, float(sum(rm["stats"]["phase_cycles"].values()))),
             "max_abs_diff_continuous_vs_finite_n": float(abs(rc["mean"] - rm["mean"]).max())}
+
+
+# ---------------------------------------------------------------- time to <Z>, ring of 32
+def tts_ring32(T, W, local, k):
+    """ring32_heisenberg_T2 (n = 32, fields U[-2, 2], T = 2, N = 8000, chi 64,
+    cutoff 1e-10, mixed precision, all <Z_i> at 20 times): K full circuits are
+    evolved and timed (one launch, persistent CTAs); the time for the workload's
+    10^4 samples is extrapolated as ceil(10^4 / K) such launches, which holds
+    while K is a multiple of the CTAs of a launch. Labelled as an extrapolation."""
+    prob, par, ex = W.workload(W.RING32)
+    run_par = W.Params(**{**par.__dict__, "n_samples": k, "sample_offset": 7_000_000})
+    ctx = T.tepai_create(local)
+    try:
+        t = time.perf_counter()
+        r = T.tepai_run(ctx, prob, run_par)
+        dt = time.perf_counter() - t
+    finally:
+        T.tepai_destroy(ctx)
+    st = r["stats"]
+    waves = math.ceil(par.n_samples / k)
+    return {"config": "ring32_heisenberg_T2 (n=32, N=8000, chi_max=64, cutoff 1e-10, mixed, <Z_i> at 20 times)",
+            "timed_samples": k, "timed_s": dt, "grid_ctas": st["grid_ctas"],
+            "events_per_sample": st["mean_nu"], "updates": st["gate_updates"] + st["swap_updates"],
+            "max_chi": st["max_chi"], "max_discarded_weight": st["max_discarded_weight"],
+            "extrapolated_time_to_Z_s": dt * waves, "extrapolation": f"{waves} launches of {k} samples",
+            "stderr_max_at_k": float(r["stderr"].max()),
+            "stderr_max_extrapolated": float(r["stderr"].max()) * math.sqrt(k / par.n_samples)}
 
 
 # ---------------------------------------------------------------- our arm
@@ -236,6 +308,8 @@ def run_ours(a):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     batch = a.batch or 16 * sms
     prob, par, init = W.bench_workload(batch, window_steps=a.window, chi=a.chi, n=a.n)
+    if a.launch_variant:
+        par = W.Params(**{**par.__dict__, "launch_variant": a.launch_variant})
     stream = torch.cuda.current_stream()
     run = T.DeviceRun(prob, par, init, stream=stream)
     base = 1_000_000 * (rank + 1)
@@ -259,7 +333,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     t0 = time.perf_counter()
-    upd, flops, kms, events, sweeps, qrm = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0
+    upd, flops, kms, events, sweeps, qrm, tcf, reorth = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0
     jpairs, jrots = 0.0, 0.0
     phases, subphases = {}, {}
     grid = 1
@@ -271,6 +345,8 @@ def run_ours(a):
         kms += ms
         upd += st["gate_updates"] + st["swap_updates"]
         flops += st["alg_flops"]
+        tcf += st["tc_flops"]
+        reorth += st["jacobi_reorth"]
         events += st["events"]
         sweeps += st["jacobi_sweeps"]
         qrm += st["qr_moves"]
@@ -319,8 +395,12 @@ def run_ours(a):
 
     if rank != 0:
         return 0
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # roofline denominators measured on this device by the library's own
+    # microbenchmarks (FP32 FMA, tcgen05 TF32), taken after the timed region
+    peaks = T.tepai_measure_peaks(local)
+    peak = peaks["fp32_tflops"]
     achieved = flops / (kms / 1e3) / 1e12
+    tc_rate = tcf / (kms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1e3 * elapsed / a.steps, "higher_is_better": True,
@@ -338,10 +418,15 @@ def run_ours(a):
         "gpu_launches": (2 + 2 * order_on) * a.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": (DRAM_BYTES_PER_UPDATE * upd / a.steps
-                                 if (n, par.chi_max) == (64, 128) else None),
-                     "peak_note": "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"},
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_note": "FP32 FMA throughput of this GPU, measured (tepai_measure_peaks); "
+                                  "achieved = algorithmic flops (736 chi^3 per square update) per second "
+                                  "of ensemble-kernel time"},
+        "tensor_pipe": {"tc_flops_per_s": tc_rate * 1e12, "tf32_peak_tflops": peaks["tf32_tflops"],
+                        "frac_of_tf32_peak": tc_rate / peaks["tf32_tflops"] if peaks["tf32_tflops"] else None,
+                        "note": "tcgen05 MMA flops issued (3xTF32: three MMAs per product) per second of "
+                                "kernel time, against the measured TF32 MMA peak"},
+        "measured_peaks": peaks,
         "stats": {"events_per_s": events / elapsed, "updates": upd, "alg_flops": flops,
                   "sweeps_per_svd": sweeps / max(upd, 1.0),
                   "qr_moves_per_update": qrm / max(upd, 1.0),
@@ -353,16 +438,20 @@ def run_ours(a):
                   "subphase_share": {k: round(v / max(sum(phases.values()), 1.0), 4)
                                      for k, v in subphases.items()},
                   "cta_busy_frac": sum(phases.values()) / max(kms / 1e3 * SM_MAX_MHZ * 1e6 * grid, 1.0),
-                  "kernel_ms": kms, "not_converged": nconv, "max_chi": maxchi, "grid_ctas": grid},
+                  "kernel_ms": kms, "not_converged": nconv, "fp64_reorth_svds": reorth,
+                  "max_chi": maxchi, "grid_ctas": grid, "tensor_core_jacobi": bool(tcf > 0)},
     }
     if not a.no_tts and world == 1:
         line["tts_ring8"] = tts_ring8(T, W, torch, local)
+    if a.tts_ring32 and world == 1:
+        line["tts_ring32"] = tts_ring32(T, W, local, a.tts_ring32)
     if not a.no_cpu_baseline and world == 1:
-        procs = max(1, min(cpu_cores(), 16))
-        u, t = oracle_sample(1, [base + 900_000 + i for i in range(procs)], procs)
-        line["cpu_baseline"] = {"value": u / t, "unit": UNIT, "cores": procs, "kind": "oracle",
-                                "sample": f"{procs} samples x 1 Trotter step of the same workload, "
-                                          f"one process (1 BLAS thread) per sample"}
+        procs = cpu_cores()
+        u, rate = oracle_sample(1, [base + 900_000 + i for i in range(procs)], procs)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
+                                "sample": f"{procs} samples x 1 Trotter step of the same workload ({u:.0f} "
+                                          f"updates), one process (1 BLAS thread) per sample on every core "
+                                          f"of the affinity mask (nproc {procs}); evolution timed, set-up not"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

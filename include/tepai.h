@@ -99,13 +99,25 @@ typedef struct {
     int precision;                 /* TEPAI_FP64 | TEPAI_MIXED */
     int launch_variant;            /* 0 = built-in launch-shape rule. When the SVD working matrix is
                                       staged from global memory: 1 = two 256-thread CTAs per SM,
-                                      2 = one 512-thread CTA per SM. When it fits in shared memory:
-                                      3, 4, 5, 6 = 64, 128, 256, 512 threads per CTA (smaller CTAs
-                                      run more samples per SM). Variants that do not apply are
-                                      ignored. tepai_autotune reports the fastest on this device. */
+                                      2 = one 512-thread CTA per SM (both with the CUDA-core Jacobi
+                                      passes), 7 = two 256-thread CTAs per SM running the Jacobi's
+                                      Gram matrices and block updates on the tensor cores (TF32
+                                      operands split in two, FP32 accumulation; TEPAI_MIXED with
+                                      chi_max <= 128, the default there). When it fits in shared
+                                      memory: 3, 4, 5, 6 = 64, 128, 256, 512 threads per CTA
+                                      (smaller CTAs run more samples per SM). Variants that do not
+                                      apply are ignored. tepai_autotune reports the fastest on this
+                                      device. */
     const unsigned char *obs_strings; /* host, n_obs x n Pauli codes per site (0 I, 1 X, 2 Y, 3 Z):
                                       observable o is the string (x)_i P_{o,i}; NULL = Z on
                                       obs_sites. Values v[s][m][o] are <psi|P|psi>/<psi|psi>. */
+    double tie_rel;                /* truncation ties (Sec. II.A keeps the largest singular values
+                                      up to chi_max): a cut never splits a group of values whose
+                                      neighbours lie within tie_rel * s_0 of each other; the whole
+                                      group is discarded. 0 = the paper's rule, where only values
+                                      equal to working precision (1e-12 s_0) are tied. A wider band
+                                      (e.g. 1e-4) makes the kept state insensitive to rounding at
+                                      nearly degenerate cuts, at the price of discarding them. */
 } tepai_params;
 
 /* Optional initial MPS shared by all samples (a "hybrid" start). Site tensors
@@ -135,22 +147,32 @@ typedef struct {
                                       none, 1 bond dimension out of range, 2 invalid singular-value
                                       ranking, 3 non-finite column norm, 4 bulk copy did not land,
                                       5 Jacobi column handoff did not arrive, 6 invalid entry in
-                                      the sample order */
+                                      the sample order, 7 tensor-core MMAs did not complete */
     double phase_cycles[8];        /* SM cycles per phase, summed over CTAs: init, sampler,
                                       single-site gates, theta, Jacobi SVD, truncation and
                                       write-back, centre moves (QR), measurement */
     int grid_ctas;                 /* CTAs of the ensemble launch */
     double jacobi_pairs;           /* column pairs examined by the Jacobi sweeps */
     double jacobi_rotations;       /* column pairs rotated by the Jacobi sweeps */
-    double subphase_cycles[8];     /* SM cycles of parts nested in the phases above: Householder
+    double subphase_cycles[12];    /* SM cycles of parts nested in the phases above: Householder
                                       panels, trailing block-reflector updates, explicit Q, R times
                                       the neighbour site, SVD projection and write-back, waits on
-                                      bulk copies, Jacobi passes, singular-value ranking */
+                                      bulk copies, Jacobi passes, singular-value ranking; and inside
+                                      the tensor-core Jacobi passes: Gram GEMMs, Gram assembly,
+                                      rotation rounds, block updates with write-back */
     int sample_order;              /* 1 when the call handed out its samples costliest first
                                       (predicted two-site updates, from the sampler's own draws):
                                       sampled variants, more samples than CTAs, at most 65536
                                       draws per sample, unless TEPAI_LPT=0. Adds two small
                                       launches per call; results do not depend on it. */
+    double seconds;                /* device time of the call's ensemble work (kernels of the
+                                      last execute, CUDA events on its stream) */
+    double mean_nu;                /* events / n_samples: mean non-identity gates per sample */
+    double jacobi_reorth;          /* mixed precision: SVDs whose FP32 Jacobi stalled (rotation
+                                      count not falling, or the sweep cap) and were finished by one
+                                      pass with FP64 inner products and rotations */
+    double tc_flops;               /* flops of the tensor-core MMAs issued (2 M N K per tcgen05.mma;
+                                      a 3xTF32 product counts three), 0 on the CUDA-core paths */
 } tepai_stats;
 
 /* Circuit event of one sample: Trotter step j (1-based), term k, setting v
@@ -254,28 +276,48 @@ int tepai_autotune(tepai_ctx *ctx, const tepai_problem *prob, const tepai_params
 
 /* ---- entry point without device allocation ------------------------------
  * The paper has no counterpart: this is a library-usage concern. Some callers
- * cannot call cudaMalloc, for example code that records a CUDA graph, a host
- * whose memory pool may not grow, or a plug-in that only receives
- * pre-allocated buffers. This call runs the same ensemble kernel as
- * tepai_sample_values, from the product state init_bits, and allocates no device memory. All of its
- * scratch (tables, counters and one MPS arena per CTA) lives in a 64 MiB
- * static device array that every GPU loading the library holds until the
- * process exits. The host-side plan lives in static storage as well.
- *   d_v    [n_samples][M][n_obs] and d_sign [n_samples][M]: caller-owned device
- *          buffers (same layout as tepai_sample_values).
- *   stream cudaStream_t (NULL = legacy default stream). The call waits for
- *          its work on the stream before it returns.
+ * cannot allocate device memory: a host application that hands each
+ * component a fixed device budget and forbids further allocations, a plug-in
+ * that only receives buffers its framework allocated, or code that must not pay
+ * cudaMalloc's implicit device synchronisation. This call runs the same
+ * ensemble kernel as tepai_sample_values, from the product state init_bits,
+ * with the same numerical settings, and allocates no device memory. All of its
+ * scratch (tables, counters and one MPS arena per CTA) lives in a 64 MiB static
+ * device array that every GPU loading the library holds until the process
+ * exits. The host-side plan lives in static storage as well.
+ *   d_v    [n_samples][M][n_obs] (double) and d_sign [n_samples][M] (int8):
+ *          caller-owned device buffers (same layout as tepai_sample_values).
+ *   stream cudaStream_t (NULL = legacy default stream). The call synchronises
+ *          the stream and copies one status word back to the host before it
+ *          returns.
  * Sizes: problems with at most 1024 spins; the MPS of one CTA must fit in the
  * array (n * 2 chi_max^2 + 8 chi_max^2 complex values), otherwise
  * TEPAI_ERR_WORKSPACE_TOO_SMALL. The number of CTAs is capped by what fits.
  * The first call on a device looks up the device address of the array
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call reuses the same array and leaves its
- * contents behind; each call clears its own counters. Calls serialise their
- * host-side part, but two calls whose GPU work overlaps (different streams or
- * threads) race on the array. */
+ * (cudaGetSymbolAddress) with that device current and keeps it; make that
+ * first call before any stream capture, and do not call this entry point on a
+ * device after cudaDeviceReset in the same process (the kept address would be
+ * stale). Every call reuses the same array and leaves its contents behind;
+ * each call clears its own counters. Calls serialise their host-side part, but
+ * two calls whose GPU work overlaps (different streams or threads) race on the
+ * array. */
 int tepai_sample_values_static(const tepai_problem *prob, const tepai_params *par,
                                double *d_v, signed char *d_sign, void *stream);
+
+/* ---- measured pipe throughput (roofline denominators) --------------------
+ * No counterpart in the paper: a measurement helper. Runs three short
+ * microbenchmarks on CUDA device `cuda_device` (each timed with CUDA events
+ * after a warm-up launch, on a stream of its own) and reports TFLOP/s:
+ *   fp32_tflops  FP32 fused multiply-add on every SM (8 independent chains per
+ *                thread), the pipe of the Jacobi rotations and Householder QR;
+ *   fp64_tflops  the same in FP64;
+ *   tf32_tflops  tcgen05.mma kind::tf32 (M = 128, N = 256, K = 8) issued back
+ *                to back by one thread per SM into TMEM, the pipe of the
+ *                tensor-core Jacobi and products (a 3xTF32 product costs three).
+ * Any output may be NULL (that benchmark is skipped). Allocates and frees a
+ * few KB of device memory. Returns TEPAI_ERR_DEVICE_CHECK if the tensor-core
+ * benchmark's bounded wait ran out. */
+int tepai_measure_peaks(int cuda_device, double *fp32_tflops, double *fp64_tflops, double *tf32_tflops);
 
 const char *tepai_strerror(int code);
 /* Text of the last CUDA error seen by this thread ("" if none). */

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtepai.so")
-SOURCES = ["ens_f32.cu", "ens_f64.cu", "aux_kernels.cu", "abi.cu", "static_scratch.cu"]
+SOURCES = ["ens_f32.cu", "ens_f64.cu", "aux_kernels.cu", "abi.cu", "static_scratch.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

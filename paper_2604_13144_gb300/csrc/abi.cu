@@ -43,16 +43,6 @@ int cuda_fail(cudaError_t e) {
 
 inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Jacobi tolerance, singular-value floor and sweep cap per precision.
-// Singular values closer than gap_rel * s_0 count as one tied group at a cut
-// (the same rule in both precisions, so that both compute the same estimator).
-struct NumCfg { double tol, floor_rel, gap_rel; int max_sweeps; int csize; };
-NumCfg num_cfg(int precision) {
-  // tol is scaled by sqrt(m) in the kernel (m = rows of the orthogonalised matrix)
-  if (precision == TEPAI_FP64) return {2 * 1.1102230246251565e-16, 1e-14, 1e-4, 60, 16};
-  return {2 * 5.9604644775390625e-08, 4e-6, 1e-4, 40, 8};
-}
-
 // Longest-first sample order: on unless TEPAI_LPT=0 (kept switchable for A/B
 // timing). It applies to sampled variants whose samples are short (at most
 // 65536 draws each), where the persistent grid's last wave is a visible share
@@ -62,13 +52,6 @@ bool lpt_applies(const HostPlan& hp, const tepai_params* Q, int grid) {
   if (e && e[0] == '0' && e[1] == 0) return false;
   if (Q->variant != TEPAI_UNBIASED && Q->variant != TEPAI_NO_PI) return false;
   return hp.run_steps * (long long)hp.L <= 65536 && Q->n_samples > grid && Q->n_samples < (1LL << 31);
-}
-
-// QR preconditioning of the Jacobi SVD: on unless TEPAI_JACOBI_PRECONDITION=0
-// (kept switchable for A/B timing of the two SVD variants).
-int jacobi_precondition() {
-  const char* e = std::getenv("TEPAI_JACOBI_PRECONDITION");
-  return (e && e[0] == '0') ? 0 : 1;
 }
 
 struct Layout {
@@ -139,6 +122,7 @@ bool is_default_stream(cudaStream_t st) {
 
 struct Prepared {
   KArgs ka;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;  // around the last execute's stream work (tepai_stats.seconds)
   int precision, grid, block;
   size_t smem;
   long long n_samples;
@@ -157,6 +141,27 @@ bool graphs_enabled() {
 
 std::mutex g_mu;
 std::unordered_map<void*, Prepared> g_reg;
+
+void prepared_free(Prepared& p) {
+  graph_free(p.g);
+  if (p.t0) cudaEventDestroy(p.t0);
+  if (p.t1) cudaEventDestroy(p.t1);
+  p.t0 = p.t1 = nullptr;
+}
+
+// Test-only knob of the bounded Jacobi column handoff: TEPAI_TEST_HANDOFF_LIMIT=k
+// gives every handoff wait k polls and a target no column reaches, so that the
+// first wait of each Jacobi pass runs out and the kernel reports device status
+// 5 (ST_HANDOFF_TIMEOUT) instead of waiting.
+void handoff_knob(KArgs& a) {
+  a.wait_limit = 0;
+  a.wait_bias = 0;
+  const char* e = std::getenv("TEPAI_TEST_HANDOFF_LIMIT");
+  if (e && e[0]) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v > 0 && v < (1L << 22)) { a.wait_limit = (int)v; a.wait_bias = 1 << 30; }
+  }
+}
 
 int launch_shape(const HostPlan& hp, const tepai_params* Q, int grid_req, LaunchShape& ls) {
   const NumCfg nc = num_cfg(Q->precision);
@@ -223,7 +228,7 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   a.n = hp.n; a.L = hp.L; a.M = hp.M; a.n_obs = hp.n_obs; a.chi_cap = Q->chi_max;
   a.periodic = hp.periodic; a.variant = Q->variant; a.max_sweeps = nc.max_sweeps;
   a.N = hp.N; a.run_steps = hp.run_steps; a.n_samples = Q->n_samples; a.sample_offset = Q->sample_offset;
-  a.seed = Q->seed; a.t_run = hp.t_run; a.cutoff = Q->cutoff; a.floor_rel = nc.floor_rel; a.tol = nc.tol; a.gap_rel = nc.gap_rel;
+  a.seed = Q->seed; a.t_run = hp.t_run; a.cutoff = Q->cutoff; a.floor_rel = nc.floor_rel; a.tol = nc.tol; a.gap_rel = tie_band(Q);
   a.terms = reinterpret_cast<const TermDev*>(base + L.terms);
   a.snaps = reinterpret_cast<const int*>(base + L.snaps);
   a.obs = reinterpret_cast<const int*>(base + L.obs);
@@ -241,8 +246,9 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
     a.cost = reinterpret_cast<int*>(base + L.cost);
     a.order = reinterpret_cast<const int*>(base + L.order);
   }
-  a.x_in_smem = ls.x_in_smem; a.smem_x_elems = ls.x_elems;
+  a.x_in_smem = ls.x_in_smem; a.smem_x_elems = ls.x_elems; a.use_tc = ls.use_tc;
   a.precondition = jacobi_precondition();
+  handoff_knob(a);
   if (init) {
     // bring the shared start state to canonical form once; every sample copies it
     a.canon = base + L.canon;
@@ -260,9 +266,11 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   pr.gnorm = reinterpret_cast<double*>(base + L.gnorm);
   pr.stats = a.stats;
   pr.stream = st;
+  CK(cudaEventCreate(&pr.t0));
+  CK(cudaEventCreate(&pr.t1));
   std::lock_guard<std::mutex> lk(g_mu);
   auto old = g_reg.find(ws);
-  if (old != g_reg.end()) graph_free(old->second.g);
+  if (old != g_reg.end()) prepared_free(old->second);
   g_reg[ws] = pr;
   return TEPAI_OK;
 }
@@ -352,8 +360,10 @@ int execute_impl(void* ws, double* d_mean, double* d_se, double* d_part, double*
     if (it == g_reg.end()) return TEPAI_ERR_INVALID_ARG;
     pr = it->second;
   }
+  if (pr.t0) CK(cudaEventRecord(pr.t0, st));
   if (!graphs_enabled()) {
     CK(enqueue_execute(pr, d_mean, d_se, d_part, d_v, d_sign, st));
+    if (pr.t1) CK(cudaEventRecord(pr.t1, st));
     return TEPAI_OK;
   }
   const void* want[5] = {d_mean, d_se, d_part, d_v, d_sign};
@@ -392,6 +402,7 @@ int execute_impl(void* ws, double* d_mean, double* d_se, double* d_part, double*
   } else {
     CK(cudaGraphLaunch(pr.g.exec, st));
   }
+  if (pr.t1) CK(cudaEventRecord(pr.t1, st));
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_reg.find(ws);
@@ -431,6 +442,13 @@ int stats_impl(void* ws, tepai_stats* out, cudaStream_t st) {
   out->jacobi_rotations = (double)ds.jac_rots;
   for (int p = 0; p < SP_N; ++p) out->subphase_cycles[p] = (double)ds.sub_cycles[p];
   out->sample_order = pr.ka.order ? 1 : 0;
+  float ms = 0.f;
+  const cudaError_t te = (pr.t0 && pr.t1) ? cudaEventElapsedTime(&ms, pr.t0, pr.t1) : cudaErrorInvalidValue;
+  out->seconds = te == cudaSuccess ? 1e-3 * ms : 0.0;
+  if (te != cudaSuccess && pr.t0 && pr.t1) cudaGetLastError();  // no timing for this execute: not an error of the call
+  out->mean_nu = pr.n_samples > 0 ? (double)ds.events / (double)pr.n_samples : 0.0;
+  out->jacobi_reorth = (double)ds.reorth;
+  out->tc_flops = ds.tc_flops;
   return TEPAI_OK;
 }
 
@@ -451,7 +469,7 @@ int ctx_reserve(tepai_ctx* c, size_t ws_bytes, size_t out_bytes) {
     if (c->ws) {
       std::lock_guard<std::mutex> lk(g_mu);
       auto it = g_reg.find(c->ws);
-    if (it != g_reg.end()) { graph_free(it->second.g); g_reg.erase(it); }
+    if (it != g_reg.end()) { prepared_free(it->second); g_reg.erase(it); }
     }
     if (c->ws) CK(cudaFree(c->ws));
     c->ws = nullptr; c->ws_bytes = 0;
@@ -527,7 +545,7 @@ void tepai_destroy(tepai_ctx* c) {
   if (c->ws) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_reg.find(c->ws);
-    if (it != g_reg.end()) { graph_free(it->second.g); g_reg.erase(it); }
+    if (it != g_reg.end()) { prepared_free(it->second); g_reg.erase(it); }
   }
   if (c->ws) cudaFree(c->ws);
   if (c->out) cudaFree(c->out);
@@ -560,7 +578,7 @@ int tepai_export_circuit(tepai_ctx* c, const tepai_problem* P, const tepai_param
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_reg.find(c->ws);
-    if (it != g_reg.end()) { graph_free(it->second.g); g_reg.erase(it); }
+    if (it != g_reg.end()) { prepared_free(it->second); g_reg.erase(it); }
   }
   char* base = static_cast<char*>(c->ws);
   CK(cudaMemcpyAsync(base, hp.terms.data(), sizeof(TermDev) * hp.L, cudaMemcpyHostToDevice, c->stream));
@@ -683,7 +701,7 @@ int tepai_dev_release(void* d_ws) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_reg.find(d_ws);
   if (it != g_reg.end()) {
-    graph_free(it->second.g);
+    prepared_free(it->second);
     g_reg.erase(it);
   }
   return TEPAI_OK;
@@ -701,9 +719,9 @@ int tepai_autotune(tepai_ctx* c, const tepai_problem* P, const tepai_params* Q, 
   if (rc) return rc;
   int best = 0;
   double best_r = -1.0;
-  LaunchShape seen[7];
+  LaunchShape seen[8];
   int n_seen = 0;
-  for (int v = 1; v <= 6; ++v) {
+  for (int v = 1; v <= 7; ++v) {
     tepai_params q = *Q;
     q.launch_variant = v;
     q.n_snapshots = 1;

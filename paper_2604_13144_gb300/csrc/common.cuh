@@ -69,7 +69,11 @@ enum : int { PH_INIT = 0, PH_SAMPLER, PH_SINGLE, PH_THETA, PH_JACOBI, PH_TRUNC, 
 // panel factorisation, trailing block-reflector updates, explicit Q, R times
 // the neighbour site, SVD projection and write-back, waits on bulk copies,
 // Jacobi passes, singular-value ranking and truncation bookkeeping.
-enum : int { SP_QR_PANEL = 0, SP_QR_APPLY, SP_QR_FORMQ, SP_QR_RMUL, SP_PROJ, SP_BULK, SP_PASSES, SP_RANK, SP_N };
+// The last four split the tensor-core Jacobi: Gram GEMMs, assembly of the
+// complex Gram matrix from TMEM, rotation rounds, block-update GEMMs and
+// write-back.
+enum : int { SP_QR_PANEL = 0, SP_QR_APPLY, SP_QR_FORMQ, SP_QR_RMUL, SP_PROJ, SP_BULK, SP_PASSES, SP_RANK,
+             SP_TC_GRAM, SP_TC_ASSEMBLE, SP_TC_ROUNDS, SP_TC_UPDATE, SP_N };
 
 struct DevStats {
   unsigned long long events, gate_updates, swap_updates, qr_moves, sweeps, not_converged;
@@ -79,6 +83,8 @@ struct DevStats {
   unsigned long long cycles[PH_N];
   unsigned long long jac_pairs, jac_rots;  // Jacobi pair checks and rotations
   unsigned long long sub_cycles[SP_N];
+  unsigned long long reorth;               // SVDs finished by the FP64 re-orthogonalisation pass
+  double tc_flops;                         // flops of the tcgen05 MMAs issued (2 M N K each)
 };
 
 struct KArgs {
@@ -110,14 +116,35 @@ struct KArgs {
   int smem_x_elems;          // capacity of that buffer (complex elements)
   int* status;               // [4]: first failure (code, detail, sample, 0); 0 = ok
   int precondition;          // 1 = QR-preconditioned Jacobi where the shapes allow it
+  int use_tc;                // 1 = tensor-core Jacobi where it applies (launch shape with its staging room)
+  int wait_limit;            // spin iterations of a Jacobi column handoff wait before it gives up
+  int wait_bias;             // added to every handoff target (0; tests set it so that no wait is met)
 };
 
 // Device status codes. A CTA that detects a broken invariant records the first
 // failure, touches no more memory for that sample, and leaves the kernel.
 enum : int { ST_OK = 0, ST_BAD_DIM = 1, ST_BAD_RANK = 2, ST_NONFINITE = 3, ST_COPY_TIMEOUT = 4, ST_HANDOFF_TIMEOUT = 5,
-             ST_BAD_ORDER = 6 };
+             ST_BAD_ORDER = 6, ST_MMA_TIMEOUT = 7 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t al) { return (x + al - 1) / al * al; }
+
+// Shared-memory plan of the tensor-core Jacobi inside the staging area (byte
+// offsets): one operand stage (A hi, A lo, B hi, B lo of 128 rows x KT FP32),
+// the 64 x 64 complex Gram matrix G (row stride GS) and the accumulated
+// rotation V; TMEM columns held by the CTA. Sized so that two 256-thread CTAs
+// share an SM.
+struct TcJac {
+  static constexpr int KT = 16;
+  static constexpr int STAGES = 1;
+  static constexpr int OP_FLOATS = 128 * KT;
+  static constexpr size_t STAGE_BYTES = 4 * OP_FLOATS * 4;
+  static constexpr int GS = 65;                 // row stride of G (complex): rows fall on distinct banks
+  static constexpr size_t G_OFF = STAGES * STAGE_BYTES;
+  static constexpr size_t V_OFF = G_OFF + 64 * GS * 8;
+  static constexpr size_t BYTES = V_OFF + 64 * 64 * 8;
+  static constexpr uint32_t TMEM_COLS = 128;
+  static constexpr int THREADS = 256;
+};
 
 // Fixed shared-memory bytes of the engine for (n, L, cap, sizeof complex).
 // n_clocks: terms with a Poisson clock (the N -> infinity sampler), else 0.

@@ -112,7 +112,9 @@ struct LocalStats {
   double max_discarded = 0.0, alg_flops = 0.0;
   unsigned long long cycles[PH_N] = {0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long jac_pairs = 0, jac_rots = 0;
-  unsigned long long sub_cycles[SP_N] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long sub_cycles[SP_N] = {};
+  unsigned long long reorth = 0;
+  double tc_flops = 0.0;
 };
 
 // Adds the SM cycles of a scope to one phase counter (thread 0 only).
@@ -236,6 +238,12 @@ struct Engine {
   int cap;            // bond-dimension cap (chi_max)
   int centre;
   LocalStats st;
+  // tensor cores: TMEM base address, the two stage mbarriers of tc_gemm and
+  // the commits issued on each (uniform across the CTA); tc_ok once TMEM is held
+  bool tc_ok = false;
+  uint32_t tmem = 0;
+  unsigned long long* tcbar = nullptr;
+  uint32_t tc_cnt[2] = {0, 0};
 
   __device__ Engine(const KArgs& args, SmemLayout s, char* arena)
       : a(args), sm(s), cap(args.chi_cap), centre(0) {
@@ -329,11 +337,12 @@ struct Engine {
     bulk_drain();
   }
   // Bounded wait until column counter *ver reaches r (every lane polls). A
-  // wait that runs out records ibuf[5] = 1 and returns; the pass then finishes
-  // without further waits and the caller fails the sample.
+  // wait that runs out (ibuf[7] polls; ibuf[8] is added to the target, 0
+  // except in tests of this path) records ibuf[5] = 1 and returns; the pass
+  // then finishes without further waits and the caller fails the sample.
   __device__ __forceinline__ void wait_col(const int* ver, int r) {
-    for (int it = 0; handoff::ld_acquire(ver) < r; ++it) {
-      if (it >= (1 << 22) || sm.ibuf[5]) { sm.ibuf[5] = 1; return; }
+    for (int it = 0; handoff::ld_acquire(ver) < r + sm.ibuf[8]; ++it) {
+      if (it >= sm.ibuf[7] || sm.ibuf[5]) { sm.ibuf[5] = 1; return; }
     }
   }
   __device__ __forceinline__ int tid() const { return threadIdx.x; }
@@ -371,6 +380,20 @@ struct Engine {
   __device__ void two_site(int i, const C g[16], bool end_left, bool is_swap);
   __device__ void form_theta(int i, const C g[16], bool end_left, bool zh, C* X);
   __device__ int jacobi(C* X, int m, int nc, bool x_in_smem);
+  __device__ int jacobi_tc(C* X, int m, int nc, R tol, R thr);
+  template <class STAGE>
+  __device__ void tc_pipeline(int N, int nch, bool same, STAGE stage);
+  template <class FA, class FB>
+  __device__ void tc_gemm(int N, int K, bool same, FA fa, FB fb);
+  template <class FA, class FB, class FO>
+  __device__ void tc_cgemm(int M, int N, int K, FA fa, FB fb, FO fo);
+  // a complex product goes to the tensor cores when the CTA holds TMEM and the
+  // product is large enough to fill 128-row tiles (below that, block_gemm)
+  __device__ bool tc_worth(int M, int N, int K) const {
+    return sizeof(R) == 4 && tc_ok && (long long)M * N * K >= 64LL * 64 * 64;
+  }
+  __device__ bool tc_wait(int s);
+  __device__ void reorth_pass_f64(C* X, int m, int nc, bool x_in_smem, double thr);
   __device__ void rr_pass(C* X, int m, int nc, R tol, R thr);
   __device__ void cross_pass(C* XA, int na, C* XB, int nb, int m, R tol, R thr);
   template <int RPL>

@@ -3,9 +3,17 @@
 
 namespace tepai {
 
+// Dynamic shared memory of the ensemble kernel, with the SM's carveout set to
+// the largest shared-memory share: the staged shapes place two CTAs of about
+// 110 KB on one SM, which the default carveout preference need not allow.
+static cudaError_t ensemble_smem_attr_f64(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(ensemble_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(ensemble_kernel<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
 cudaError_t launch_ensemble_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(ensemble_kernel<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensemble_smem_attr_f64(smem);
   if (e != cudaSuccess) return e;
   ensemble_kernel<double><<<grid, block, smem, st>>>(a);
   return cudaGetLastError();
@@ -21,9 +29,7 @@ cudaError_t launch_ensemble_captured_f64(const KArgs& a, int grid, int block, si
 // The kernel's address, to find its node in a captured CUDA graph.
 const void* ensemble_kernel_fn_f64() { return reinterpret_cast<const void*>(ensemble_kernel<double>); }
 
-cudaError_t set_ensemble_smem_f64(size_t smem) {
-  return cudaFuncSetAttribute(ensemble_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
+cudaError_t set_ensemble_smem_f64(size_t smem) { return ensemble_smem_attr_f64(smem); }
 
 cudaError_t launch_canon_f64(const KArgs& a, int block, size_t smem, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(canon_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -33,8 +39,7 @@ cudaError_t launch_canon_f64(const KArgs& a, int block, size_t smem, cudaStream_
 }
 
 cudaError_t occupancy_ensemble_f64(int block, size_t smem, int* ctas_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(ensemble_kernel<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensemble_smem_attr_f64(smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, ensemble_kernel<double>, block, smem);
 }

@@ -4,6 +4,8 @@
 #pragma once
 #include "qr.cuh"
 #include "svd_update.cuh"
+#include "tc_gemm.cuh"
+#include "jacobi_tc.cuh"
 
 namespace tepai {
 
@@ -570,14 +572,26 @@ template <typename R>
 __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_next;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) unsigned long long s_tcbar[2];
   SmemLayout sm = carve_smem(smem_raw, a, (int)sizeof(cplx<R>));
   char* arena = a.arena + (size_t)blockIdx.x * a.arena_stride;
   Engine<R> eng(a, sm, arena);
+  // single precision with the tensor-core launch shape: hold TMEM for the
+  // whole kernel (one warp allocates and, at the end, frees it)
+  const bool use_tc = sizeof(R) == 4 && a.use_tc && blockDim.x >= 128;
+  if (use_tc && threadIdx.x < 32) { tc::alloc(&s_tmem, TcJac::TMEM_COLS); tc::relinquish(); }
   if (threadIdx.x == 0) {
     sm.ibuf[13] = 0; sm.ibuf[14] = 0; sm.ibuf[15] = 0;
+    sm.ibuf[7] = a.wait_limit > 0 ? a.wait_limit : (1 << 22);
+    sm.ibuf[8] = a.wait_bias > 0 ? a.wait_bias : 0;
     for (int b = 0; b < 3; ++b) bulk::mbar_init(sm.mbar + b);
+    if (use_tc) { bulk::mbar_init(s_tcbar); bulk::mbar_init(s_tcbar + 1); }
   }
+  tc::fence_before();
   __syncthreads();
+  tc::fence_after();
+  if (use_tc) { eng.tc_ok = true; eng.tmem = s_tmem; eng.tcbar = s_tcbar; }
   while (!eng.failed()) {
     if (threadIdx.x == 0) {
       // queue slot -> sample: with an order, the costliest samples go first
@@ -649,6 +663,21 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
     atomicAdd(&a.stats->jac_pairs, st.jac_pairs);
     atomicAdd(&a.stats->jac_rots, st.jac_rots);
     for (int p = 0; p < SP_N; ++p) atomicAdd(&a.stats->sub_cycles[p], st.sub_cycles[p]);
+    atomicAdd(&a.stats->reorth, st.reorth);
+    atomicAdd(&a.stats->tc_flops, st.tc_flops);
+  }
+  if (use_tc) {
+    // no MMA may still be writing TMEM when it is freed: bounded waits for the
+    // latest commit on each stage barrier (already complete unless a wait
+    // timed out), then the allocating warp frees the columns
+    for (int s = 0; s < 2; ++s) {
+      if (eng.tc_cnt[s] == 0) continue;
+      bool ok = false;
+      for (int it = 0; it < (1 << 24) && !ok; ++it) ok = bulk::try_wait(s_tcbar + s, (eng.tc_cnt[s] - 1) & 1u);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::dealloc(eng.tmem, TcJac::TMEM_COLS);
   }
 }
 
@@ -663,6 +692,7 @@ __global__ void __launch_bounds__(512, 1) canon_kernel(const __grid_constant__ K
   Engine<R> eng(a, sm, const_cast<char*>(a.canon));
   if (threadIdx.x == 0) {
     sm.ibuf[13] = 0; sm.ibuf[14] = 0; sm.ibuf[15] = 0;
+    sm.ibuf[7] = 1 << 22; sm.ibuf[8] = 0;
     for (int b = 0; b < 3; ++b) bulk::mbar_init(sm.mbar + b);
   }
   __syncthreads();

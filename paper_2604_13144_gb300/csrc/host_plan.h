@@ -6,12 +6,34 @@
 #include <cmath>
 #include <complex>
 #include <cstdint>
+#include <cstdlib>
 #include <vector>
 
 #include "../../include/tepai.h"
 #include "common.cuh"
 
 namespace tepai {
+
+// Jacobi tolerance (scaled by sqrt(m) in the kernel, m = rows of the
+// orthogonalised matrix), singular-value floor (values at or below
+// floor_rel * s_0 are zero to working precision), sweep cap and complex
+// element size per precision.
+struct NumCfg { double tol, floor_rel; int max_sweeps; int csize; };
+inline NumCfg num_cfg(int precision) {
+  if (precision == TEPAI_FP64) return {2 * 1.1102230246251565e-16, 1e-14, 60, 16};
+  return {2 * 5.9604644775390625e-08, 4e-6, 40, 8};
+}
+
+// Tie band at truncation cuts: the caller's tie_rel, else the paper's rule
+// (only values equal to working precision, 1e-12 s_0, are tied).
+inline double tie_band(const tepai_params* Q) { return Q->tie_rel > 0.0 ? Q->tie_rel : 1e-12; }
+
+// QR preconditioning of the Jacobi SVD: on unless TEPAI_JACOBI_PRECONDITION=0
+// (kept switchable for A/B timing of the two SVD variants).
+inline int jacobi_precondition() {
+  const char* e = std::getenv("TEPAI_JACOBI_PRECONDITION");
+  return (e && e[0] == '0') ? 0 : 1;
+}
 
 // Fixed-capacity vector for plans that must not touch the heap.
 template <typename T, size_t N>
@@ -132,9 +154,10 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   if (!(std::isfinite(Q->T) && Q->T >= 0.0) || Q->n_steps < 1) return TEPAI_ERR_INVALID_ARG;
   if (!(std::isfinite(Q->delta) && Q->delta > 0.0)) return TEPAI_ERR_INVALID_ARG;
   if (Q->chi_max < 1 || !(std::isfinite(Q->cutoff) && Q->cutoff >= 0.0)) return TEPAI_ERR_INVALID_ARG;
+  if (!(std::isfinite(Q->tie_rel) && Q->tie_rel >= 0.0 && Q->tie_rel < 1.0)) return TEPAI_ERR_INVALID_ARG;
   if (Q->variant < 0 || Q->variant > 3 || Q->precision < 0 || Q->precision > 1) return TEPAI_ERR_INVALID_ARG;
   if (Q->variant == TEPAI_CONTINUOUS && !(Q->delta < M_PI)) return TEPAI_ERR_INVALID_ARG;
-  if (Q->launch_variant < 0 || Q->launch_variant > 6) return TEPAI_ERR_INVALID_ARG;
+  if (Q->launch_variant < 0 || Q->launch_variant > 7) return TEPAI_ERR_INVALID_ARG;
   if (Q->n_samples < 0 || Q->sample_offset < 0) return TEPAI_ERR_INVALID_ARG;
   const long long S = Q->run_steps ? Q->run_steps : Q->n_steps;
   if (S < 1 || S > Q->n_steps) return TEPAI_ERR_INVALID_ARG;
@@ -265,23 +288,27 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
 
 // Launch shape of the ensemble kernel: threads per CTA, dynamic shared memory,
 // where the SVD working matrix lives, and resident CTAs per SM (per_sm).
-struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems, per_sm; };
+struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems, per_sm, use_tc; };
 
 // Picks the shape for bond cap `cap` and complex size `csize` bytes. `occ`
 // reports resident CTAs per SM of a (block, smem) pair. When the whole SVD
 // working matrix (2cap x 2cap) fits in shared memory it stays there; otherwise
-// it lives in global memory and column blocks are staged. Staged shapes first
-// try two samples per SM (256 threads each, staging room for a 16-column
-// Householder panel and one 16-column update chunk, which also holds two
-// 16-column Jacobi blocks): two independent CTAs fill each other's barrier,
-// latency and copy-wait stalls, and the modest staging leaves L1 room for
-// the global operands. If two do not fit, one 512-thread CTA per SM stages
-// blocks within 128 KB.
+// it lives in global memory and column blocks are staged.
+//   - Single precision with at most 256 rows (cap <= 128): 256-thread CTAs,
+//     two per SM, whose staging room holds the tensor-core Jacobi's operand
+//     stage, Gram matrix and rotation (TcJac::BYTES); each CTA holds TMEM.
+//   - Otherwise staged shapes first try two samples per SM (256 threads each,
+//     staging room for a 16-column Householder panel and one 16-column update
+//     chunk, which also holds two 16-column Jacobi blocks): two independent
+//     CTAs fill each other's barrier, latency and copy-wait stalls, and the
+//     modest staging leaves L1 room for the global operands. If two do not
+//     fit, one 512-thread CTA per SM stages blocks within 128 KB.
 // `variant` forces a shape. For a staged working matrix: 1 = two 256-thread
-// CTAs per SM, 2 = one 512-thread CTA per SM. For a working matrix held in
-// shared memory: 3, 4, 5, 6 = 64, 128, 256, 512 threads per CTA, so that small
-// bond dimensions run several samples per SM. 0 (or a variant that does not
-// apply) keeps the rule.
+// CTAs per SM, 2 = one 512-thread CTA per SM (both with the CUDA-core Jacobi
+// passes), 7 = the tensor-core shape. When the working matrix fits in shared
+// memory: 3, 4, 5, 6 = 64, 128, 256, 512 threads per CTA (smaller CTAs at small
+// bond dimensions run several samples per SM). 0 (or a variant that does not
+// apply) = the rule above.
 template <class Occ>
 inline cudaError_t choose_launch_shape(int n, int L, int n_clocks, int cap, int csize, int optin, Occ occ,
                                        LaunchShape& ls, int variant = 0) {
@@ -289,11 +316,20 @@ inline cudaError_t choose_launch_shape(int n, int L, int n_clocks, int cap, int 
   const size_t xbytes = (size_t)4 * cap * cap * csize;
   int per_sm = 1;
   cudaError_t e;
+  ls.use_tc = 0;
   if (fixed + xbytes <= (size_t)optin) {
     ls.block = variant >= 3 && variant <= 6 ? (64 << (variant - 3)) : (cap >= 64 ? 512 : 256);
     ls.x_in_smem = 1;
     ls.x_elems = 4 * cap * cap;
     ls.smem = fixed + xbytes;
+    e = occ(ls.block, ls.smem, &per_sm);
+  } else if (csize == 8 && 2 * cap <= 256 && (variant == 0 || variant == 7) &&
+             fixed + align_up(TcJac::BYTES, 8) <= (size_t)optin) {
+    ls.block = TcJac::THREADS;
+    ls.x_in_smem = 0;
+    ls.x_elems = (int)(align_up(TcJac::BYTES, 8) / 8);
+    ls.smem = fixed + (size_t)ls.x_elems * 8;
+    ls.use_tc = 1;
     e = occ(ls.block, ls.smem, &per_sm);
   } else {
     ls.block = 256;

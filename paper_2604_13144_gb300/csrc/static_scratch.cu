@@ -1,9 +1,10 @@
 // tepai_sample_values_static: the ensemble run for callers that cannot
-// allocate device memory. Examples are code that must not call cudaMalloc
-// while a CUDA graph is being built, hosts whose memory pool forbids growth, and
-// plug-ins that only receive pre-allocated buffers. All scratch of this entry point
-// lives in one file-scope device array of fixed size; the caller passes the
-// output buffers.
+// allocate device memory themselves or through the library: a host that hands
+// each component a fixed device budget and forbids further allocations, a
+// plug-in that only receives buffers its framework allocated, or code that must
+// not pay cudaMalloc's implicit device synchronisation on its path. All scratch
+// of this entry point lives in one file-scope device array of fixed size; the
+// caller passes the output buffers.
 #include <cstring>
 #include <mutex>
 
@@ -36,7 +37,10 @@ FixedPlan g_static_plan;
 inline size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Device address of the scratch array on the current device, looked up once
-// per device (with that device current).
+// per device (with that device current) and kept for the life of the process.
+// cudaDeviceReset unloads the module that holds the array, so the kept address
+// is stale after it: a process that resets a device must not call this entry
+// point again on that device.
 int static_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -113,12 +117,13 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
   KArgs a{};
   a.n = hp.n; a.L = hp.L; a.M = hp.M; a.n_obs = hp.n_obs; a.chi_cap = cap;
   a.periodic = hp.periodic; a.variant = Q->variant;
-  a.max_sweeps = Q->precision == TEPAI_FP64 ? 60 : 40;
+  const NumCfg nc = num_cfg(Q->precision);
+  a.max_sweeps = nc.max_sweeps;
   a.N = hp.N; a.run_steps = hp.run_steps; a.n_samples = Q->n_samples; a.sample_offset = Q->sample_offset;
   a.seed = Q->seed; a.t_run = hp.t_run; a.cutoff = Q->cutoff;
-  a.floor_rel = Q->precision == TEPAI_FP64 ? 1e-14 : 4e-6;
-  a.tol = Q->precision == TEPAI_FP64 ? 2 * 1.1102230246251565e-16 : 2 * 5.9604644775390625e-08;
-  a.gap_rel = 1e-4;
+  a.floor_rel = nc.floor_rel;
+  a.tol = nc.tol;
+  a.gap_rel = tie_band(Q);
   a.terms = reinterpret_cast<const TermDev*>(base + o_terms);
   a.snaps = reinterpret_cast<const int*>(base + o_snaps);
   a.obs = reinterpret_cast<const int*>(base + o_obs);
@@ -129,8 +134,8 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
   a.stats = reinterpret_cast<DevStats*>(base + o_stats);
   a.counter = reinterpret_cast<unsigned long long*>(base + o_counter);
   a.status = reinterpret_cast<int*>(base + o_status);
-  a.x_in_smem = x_in_smem; a.smem_x_elems = x_elems;
-  a.precondition = 1;
+  a.x_in_smem = x_in_smem; a.smem_x_elems = x_elems; a.use_tc = ls.use_tc;
+  a.precondition = jacobi_precondition();
   const cudaError_t le = Q->precision == TEPAI_FP64 ? launch_ensemble_f64(a, (int)grid, block, smem, st)
                                                     : launch_ensemble_f32(a, (int)grid, block, smem, st);
   if (le != cudaSuccess) return TEPAI_ERR_CUDA;

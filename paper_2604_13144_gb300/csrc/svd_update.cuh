@@ -25,10 +25,11 @@ __device__ __noinline__ void Engine<R>::form_theta(int i, const C g[16], bool en
   const bool use_gemm = a.smem_x_elems >= gemm_tile_elems(nt()) && X != TH;
   if (use_gemm) {
     C* thp = TH;
-    block_gemm<R>(m, ncol, dc, reinterpret_cast<C*>(sm.x),
-        [=](int ii, int kk) { return A[(size_t)ii * dc + kk]; },
-        [=](int kk, int jj) { return B[(size_t)kk * ncol + jj]; },
-        [=](int ii, int jj, C v) { thp[(size_t)ii * ncol + jj] = v; });
+    auto fa = [=](int ii, int kk) { return A[(size_t)ii * dc + kk]; };
+    auto fb = [=](int kk, int jj) { return B[(size_t)kk * ncol + jj]; };
+    auto fo = [=](int ii, int jj, C v) { thp[(size_t)ii * ncol + jj] = v; };
+    if (tc_worth(m, ncol, dc)) tc_cgemm(m, ncol, dc, fa, fb, fo);
+    else block_gemm<R>(m, ncol, dc, reinterpret_cast<C*>(sm.x), fa, fb, fo);
     __syncthreads();
   }
   for (int e = tid(); e < dl * dr; e += nt()) {
@@ -180,8 +181,8 @@ __device__ __noinline__ void rr_pass_f32(float2* X, int m, int nc, float tol, fl
   const bool o0 = t0 < half, o1 = t1 < half;
   const float2 zero = make_float2(0.f, 0.f);
   auto wait = [&](const int* vp, int need) {
-    for (int it = 0; handoff::ld_acquire(vp) < need; ++it) {
-      if (it >= (1 << 22) || ibuf[5]) { ibuf[5] = 1; return; }
+    for (int it = 0; handoff::ld_acquire(vp) < need + ibuf[8]; ++it) {
+      if (it >= ibuf[7] || ibuf[5]) { ibuf[5] = 1; return; }
     }
   };
   auto slot = [&](int t, int r, int& p, int& q) {
@@ -376,8 +377,8 @@ __device__ __noinline__ void cross_pass_f32(float2* XA, int na, float2* XB, int 
     a1[t] = (h1 && in) ? XA[(size_t)p1 * m + row] : zero;
   }
   auto wait = [&](const int* vp, int need) {
-    for (int it = 0; handoff::ld_acquire(vp) < need; ++it) {
-      if (it >= (1 << 22) || ibuf[5]) { ibuf[5] = 1; return; }
+    for (int it = 0; handoff::ld_acquire(vp) < need + ibuf[8]; ++it) {
+      if (it >= ibuf[7] || ibuf[5]) { ibuf[5] = 1; return; }
     }
   };
   const int gap = nbp - nw;
@@ -641,6 +642,14 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
   nc = n_act;
   int sweep = 0;
   if (nc < 2) { __syncthreads(); if (tid() == 0) sm.ibuf[1] = 1; __syncthreads(); return 0; }
+  if constexpr (sizeof(R) == 4) {
+    // single precision, staged in global memory, up to 256 rows and more than
+    // one 32-column block: Gram matrices and block updates on the tensor cores
+    if (tc_ok && nt() == TcJac::THREADS && !x_in_smem && m <= 256 && nc > 32) {
+      SubTimer spt(st, SP_PASSES);
+      return jacobi_tc(X, m, nc, tol, thr);
+    }
+  }
   C* xs = reinterpret_cast<C*>(sm.x);
   // column blocks of bw: the width the staging buffer allows, at most 2 columns
   // per warp so that a block's warp-owned columns fit in registers
@@ -662,6 +671,7 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
     else cross_pass(XA, na, XB, nbb, m, tol, thr);
   };
   SubTimer spt(st, SP_PASSES);
+  int prev_rot = 1 << 30;   // no stall test before the second sweep
   while (sweep < a.max_sweeps) {
     if (tid() == 0) { sm.ibuf[0] = 0; sm.ibuf[6] = 0; }
     __syncthreads();
@@ -714,9 +724,66 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
     if (tid() == 0) { st.jac_rots += (unsigned long long)rot; st.jac_pairs += (unsigned long long)sm.ibuf[6]; }
     __syncthreads();
     if (rot == 0) { if (tid() == 0) sm.ibuf[1] = 1; break; }
+    // Single precision: near convergence (fewer than 1 in 20 pairs rotating)
+    // a rotation count that stops falling means the FP32 inner products are
+    // deciding on their own rounding; one pass in FP64 arithmetic then
+    // finishes the SVD, as it does at the sweep cap.
+    if constexpr (sizeof(R) == 4) {
+      if ((rot >= prev_rot && 20 * rot < sm.ibuf[6]) || sweep >= a.max_sweeps) {
+        reorth_pass_f64(X, m, nc, x_in_smem, (double)thr);
+        if (tid() == 0) { st.reorth++; sm.ibuf[1] = 1; }
+        __syncthreads();
+        break;
+      }
+    }
+    prev_rot = rot;
   }
   __syncthreads();
   return sweep;
+}
+
+// The FP64 re-orthogonalisation pass of a single-precision Jacobi whose FP32
+// residual stalled: one cyclic round-robin pass (Brent & Luk order, rounds
+// separated by CTA barriers, one warp per pair) over the nc active columns of
+// X, with FP64 inner products, FP64 rotation parameters and the rotation
+// evaluated in FP64 before the columns are rounded back to FP32. A pair is
+// rotated when its cosine exceeds 2^-24, the orthogonality FP32 columns can
+// hold, and both columns lie at or above thr. X is in shared memory or, when
+// staged, in global memory with every bulk copy already drained.
+template <typename R>
+__device__ __noinline__ void Engine<R>::reorth_pass_f64(C* X, int m, int nc, bool x_in_smem, double thr) {
+  const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
+  const int np = nc + (nc & 1);
+  const double tol = 5.9604644775390625e-08;
+  for (int r = 0; r < np - 1; ++r) {
+    for (int t = w; t < np / 2; t += nw) {
+      int p, q;
+      if (t == 0) { p = np - 1; q = r; }
+      else { p = (r + t) % (np - 1); q = (r - t + np - 1) % (np - 1); }
+      if (p >= nc || q >= nc) continue;
+      C* xp = X + (size_t)p * m;
+      C* xq = X + (size_t)q * m;
+      double al = 0, be = 0, gr = 0, gi = 0;
+      for (int row = lane; row < m; row += 32) {
+        const C u = ld_x(xp + row, x_in_smem), v = ld_x(xq + row, x_in_smem);
+        const double ur = u.re, ui = u.im, vr = v.re, vi = v.im;
+        al = fma(ur, ur, fma(ui, ui, al));
+        be = fma(vr, vr, fma(vi, vi, be));
+        gr = fma(ur, vr, fma(ui, vi, gr));
+        gi = fma(ur, vi, fma(-ui, vr, gi));
+      }
+      al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+      double c, sn, er, ei;
+      if (!rot_params<double>(al, be, gr, gi, tol, thr, c, sn, er, ei)) continue;
+      for (int row = lane; row < m; row += 32) {
+        const C u = ld_x(xp + row, x_in_smem), v = ld_x(xq + row, x_in_smem);
+        const double wr = er * (double)v.re - ei * (double)v.im, wi = er * (double)v.im + ei * (double)v.re;
+        xp[row] = C{(R)(c * (double)u.re - sn * wr), (R)(c * (double)u.im - sn * wi)};
+        xq[row] = C{(R)(sn * (double)u.re + c * wr), (R)(sn * (double)u.im + c * wi)};
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // Gate on bond (i, i+1). The centre is first moved onto site i or i+1, so that
@@ -891,10 +958,11 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
     if (a.smem_x_elems >= gemm_tile_elems(nt())) {
       // Bi = renorm U^H theta' (the working matrix in shared memory is no longer needed)
       const C* thp = TH;
-      block_gemm<R>(k, ncol, m, reinterpret_cast<C*>(sm.x),
-          [=](int ii, int kk) { const C u = Ai[(size_t)kk * k + ii]; return C{u.re, -u.im}; },
-          [=](int kk, int jj) { return thp[(size_t)kk * ncol + jj]; },
-          [=](int ii, int jj, C v) { Bi[(size_t)ii * ncol + jj] = scale(v, renorm); });
+      auto fa = [=](int ii, int kk) { const C u = Ai[(size_t)kk * k + ii]; return C{u.re, -u.im}; };
+      auto fb = [=](int kk, int jj) { return thp[(size_t)kk * ncol + jj]; };
+      auto fo = [=](int ii, int jj, C v) { Bi[(size_t)ii * ncol + jj] = scale(v, renorm); };
+      if (tc_worth(k, ncol, m)) tc_cgemm(k, ncol, m, fa, fb, fo);
+      else block_gemm<R>(k, ncol, m, reinterpret_cast<C*>(sm.x), fa, fb, fo);
     } else {
       for (int e = tid(); e < k * ncol; e += nt()) {
         const int mm = e / ncol, col = e - mm * ncol;
@@ -924,10 +992,11 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
       // Ai = renorm theta' V (V^H = Bi)
       const C* thp = TH;
       const C* bip = Bi;
-      block_gemm<R>(rows, k, ncol, reinterpret_cast<C*>(sm.x),
-          [=](int ii, int kk) { return thp[(size_t)ii * ncol + kk]; },
-          [=](int kk, int jj) { const C u = bip[(size_t)jj * ncol + kk]; return C{u.re, -u.im}; },
-          [=](int ii, int jj, C v) { Ai[(size_t)ii * k + jj] = scale(v, renorm); });
+      auto fa = [=](int ii, int kk) { return thp[(size_t)ii * ncol + kk]; };
+      auto fb = [=](int kk, int jj) { const C u = bip[(size_t)jj * ncol + kk]; return C{u.re, -u.im}; };
+      auto fo = [=](int ii, int jj, C v) { Ai[(size_t)ii * k + jj] = scale(v, renorm); };
+      if (tc_worth(rows, k, ncol)) tc_cgemm(rows, k, ncol, fa, fb, fo);
+      else block_gemm<R>(rows, k, ncol, reinterpret_cast<C*>(sm.x), fa, fb, fo);
     } else {
       for (int e = tid(); e < rows * k; e += nt()) {
         const int row = e / k, mm = e - row * k;

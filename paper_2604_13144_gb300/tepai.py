@@ -22,7 +22,7 @@ EXPORTED = ["tepai_create", "tepai_destroy", "tepai_run", "tepai_sample_values",
             "tepai_export_circuit", "tepai_gnorm", "tepai_dev_workspace_size",
             "tepai_dev_prepare", "tepai_dev_execute", "tepai_dev_set_sample_offset",
             "tepai_dev_stats", "tepai_dev_release", "tepai_autotune", "tepai_evolve_state",
-            "tepai_sample_values_static",
+            "tepai_sample_values_static", "tepai_measure_peaks",
             "tepai_strerror", "tepai_last_cuda_error"]
 
 
@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("run_steps", C.c_longlong), ("chi_max", C.c_int), ("cutoff", C.c_double),
                 ("n_snapshots", C.c_int), ("obs_sites", C.POINTER(C.c_int)), ("n_obs", C.c_int),
                 ("seed", C.c_ulonglong), ("variant", C.c_int), ("precision", C.c_int),
-                ("launch_variant", C.c_int), ("obs_strings", C.POINTER(C.c_ubyte))]
+                ("launch_variant", C.c_int), ("obs_strings", C.POINTER(C.c_ubyte)),
+                ("tie_rel", C.c_double)]
 
 
 class Mps(C.Structure):
@@ -61,12 +62,13 @@ class Stats(C.Structure):
                 ("max_chi", C.c_int), ("n_not_converged", C.c_int),
                 ("device_status", C.c_int * 3), ("phase_cycles", C.c_double * 8),
                 ("grid_ctas", C.c_int), ("jacobi_pairs", C.c_double),
-                ("jacobi_rotations", C.c_double), ("subphase_cycles", C.c_double * 8),
-                ("sample_order", C.c_int)]
+                ("jacobi_rotations", C.c_double), ("subphase_cycles", C.c_double * 12),
+                ("sample_order", C.c_int), ("seconds", C.c_double), ("mean_nu", C.c_double),
+                ("jacobi_reorth", C.c_double), ("tc_flops", C.c_double)]
 
     PHASES = ("init", "sampler", "single_site", "theta", "jacobi", "truncate", "qr", "measure")
     SUBPHASES = ("qr_panel", "qr_apply", "qr_formq", "qr_rmul", "projection", "bulk_wait",
-                 "jacobi_passes", "rank")
+                 "jacobi_passes", "rank", "tc_gram", "tc_assemble", "tc_rounds", "tc_update")
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -103,6 +105,7 @@ def _load():
         "tepai_autotune": (i, [vp, pP, pQ, pM, ll, C.POINTER(i), pd]),
         "tepai_evolve_state": (i, [vp, pP, pQ, pM, C.POINTER(i), pd, ll, C.POINTER(ll)]),
         "tepai_sample_values_static": (i, [pP, pQ, vp, vp, vp]),
+        "tepai_measure_peaks": (i, [i, pd, pd, pd]),
         "tepai_strerror": (C.c_char_p, [i]),
         "tepai_last_cuda_error": (C.c_char_p, []),
     }
@@ -153,7 +156,7 @@ class Marshalled:
                           int(par.seed) & (2**64 - 1), int(getattr(par, "variant", 0)),
                           int(getattr(par, "precision", 0)), int(getattr(par, "launch_variant", 0)),
                           self.strings.ctypes.data_as(C.POINTER(C.c_ubyte)) if self.strings is not None
-                          else None)
+                          else None, float(getattr(par, "tie_rel", 0.0)))
         self.n_obs = nobs if (obs is not None or self.strings is not None) else int(prob.n)
         self.M = int(par.n_snapshots)
         self.init = None
@@ -315,12 +318,34 @@ class DeviceRun:
             pass
 
 
+def tepai_measure_peaks(device: int = 0) -> dict:
+    """Measured FP32-FMA, FP64-FMA and tcgen05 TF32 throughput of this device
+    (TFLOP/s), from the library's own microbenchmarks."""
+    f32, f64, t32 = C.c_double(), C.c_double(), C.c_double()
+    _check(_lib.tepai_measure_peaks(int(device), C.byref(f32), C.byref(f64), C.byref(t32)),
+           "tepai_measure_peaks")
+    return {"fp32_tflops": f32.value, "fp64_tflops": f64.value, "tf32_tflops": t32.value}
+
+
+def _check_device_out(t, dtype: str, numel: int, name: str):
+    """A caller-owned output the kernel writes directly: it must be a contiguous
+    CUDA tensor of the right dtype and exactly the right size, or the call is
+    refused before any device work."""
+    ok = (getattr(t, "is_cuda", False) and str(t.dtype) == f"torch.{dtype}" and t.is_contiguous()
+          and int(t.numel()) == numel)
+    if not ok:
+        raise TepaiError(1, f"tepai_sample_values_static: {name} must be a contiguous CUDA {dtype} "
+                            f"tensor of {numel} elements")
+
+
 def tepai_sample_values_static(prob, par, d_v, d_sign, stream=None):
     """Per-sample values into caller-owned device tensors d_v (float64,
     [n_samples][M][n_obs]) and d_sign (int8, [n_samples][M]); the library
     allocates no device memory for this call (its scratch is a fixed static
     device array)."""
     m = Marshalled(prob, par)
+    _check_device_out(d_v, "float64", int(par.n_samples) * m.M * m.n_obs, "d_v")
+    _check_device_out(d_sign, "int8", int(par.n_samples) * m.M, "d_sign")
     st = stream.cuda_stream if stream is not None else None
     _check(_lib.tepai_sample_values_static(C.byref(m.prob), C.byref(m.par),
                                            C.c_void_p(d_v.data_ptr()), C.c_void_p(d_sign.data_ptr()),

@@ -61,10 +61,15 @@ def test_invalid_arguments_are_rejected(T):
     with pytest.raises(T.TepaiError):
         T.tepai_gnorm(p2, par)
     bad = W.Params(**par.__dict__)
-    bad.launch_variant = 7                                  # variants are 0 .. 6
+    bad.launch_variant = 8                                  # variants are 0 .. 7
     with pytest.raises(T.TepaiError) as e:
         T.tepai_gnorm(prob, bad)
     assert e.value.code == 1
+    for tie in (-1e-4, float("nan"), 1.0):                  # tie band must lie in [0, 1)
+        bad = W.Params(**{**par.__dict__, "tie_rel": tie})
+        with pytest.raises(T.TepaiError) as e:
+            T.tepai_gnorm(prob, bad)
+        assert e.value.code == 1
     trot = W.Params(**{**par.__dict__, "n_steps": 100, "variant": 2})   # Trotter has no Delta bound
     g, nu = T.tepai_gnorm(prob, trot)
     assert np.all(g == 1.0) and nu == 100 * 32

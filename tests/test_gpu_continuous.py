@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle_rule import oracle_rule
 from oracle import estimator, planner, sampler
 from oracle import run as oracle_run
 
@@ -42,8 +43,7 @@ def P(**kw):
 
 def _compare(T, ctx, prob, par, tol, use_sv=False):
     got = T.tepai_sample_values(ctx, prob, par)
-    floor_rel, gap_rel = (1e-14, 1e-4) if par.precision == 0 else (4e-6, 1e-4)
-    ref = oracle_run.run(prob, par, use_statevector=use_sv, floor_rel=floor_rel, gap_rel=gap_rel)
+    ref = oracle_run.run(prob, par, use_statevector=use_sv, **oracle_rule(par))
     assert np.array_equal(got["sign"], ref["sign"])
     assert got["stats"]["events"] == int(np.sum(ref["nu"]))
     err = float(np.max(np.abs(got["v"] - ref["v"])))

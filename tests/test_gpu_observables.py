@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle_rule import oracle_rule
 from oracle import run as oracle_run
 
 pytestmark = pytest.mark.gpu
@@ -83,5 +84,5 @@ def test_pauli_strings_mixed_from_random_mps(T, ctx):
     par = W.Params(T=0.05, n_steps=16, delta=math.pi / 64, n_samples=3, chi_max=64, cutoff=1e-10,
                    n_snapshots=2, seed=4, precision=1, obs_strings=strings)
     got = T.tepai_sample_values(ctx, prob, par, init)
-    want = oracle_run.run(prob, par, init_tensors=init[0], floor_rel=4e-6, gap_rel=1e-4)
+    want = oracle_run.run(prob, par, init_tensors=init[0], **oracle_rule(par))
     assert float(np.max(np.abs(got["v"] - want["v"]))) <= 1e-4

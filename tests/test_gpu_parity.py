@@ -2,11 +2,13 @@
 seeded circuits. Tolerances: 1e-10 on every <Z_i> in FP64 mode and 1e-4 in
 mixed mode; the sampler and the signs are bit-exact."""
 import math
+import os
 
 import numpy as np
 import pytest
 
 import workloads as W
+from oracle_rule import oracle_rule
 from oracle import estimator, planner, sampler
 from oracle import run as oracle_run
 from oracle import statevector as sv
@@ -53,10 +55,8 @@ def test_device_sampler_matches_oracle(T, ctx, cfg, variant):
 # ------------------------------------------------------------------ FP64 parity
 def _compare(T, ctx, prob, par, tol, init=None, use_sv=False):
     got = T.tepai_sample_values(ctx, prob, par, init)
-    # truncation-rule parameters of the library's precision mode
-    floor_rel, gap_rel = (1e-14, 1e-4) if par.precision == 0 else (4e-6, 1e-4)
     ref = oracle_run.run(prob, par, init_tensors=None if init is None else init[0],
-                         use_statevector=use_sv, floor_rel=floor_rel, gap_rel=gap_rel)
+                         use_statevector=use_sv, **oracle_rule(par))
     err = float(np.max(np.abs(got["v"] - ref["v"])))
     assert np.array_equal(got["sign"], ref["sign"])
     assert err <= tol, err
@@ -84,50 +84,45 @@ def test_fp64_ring8_samples_match_statevector(T, ctx):
     _compare(T, ctx, prob, par, TOL64, use_sv=True)
 
 
-def _compare_truncated(T, ctx, prob, par, tol, init=None):
-    """Truncated runs. A truncated trajectory can amplify rounding: each
-    sample's amplification is measured on the oracle itself, by rerunning it in
-    another exact gauge (centre moved back after every update) and taking the
-    largest change d_s of any <Z_i>. Per sample the bound is
-      FP64:  max(tol, 10 d_s)
-      mixed: max(tol, 1e10 d_s)   (FP32 SVD rounding ~1e-6 against ~1e-16)
-    At least half of the samples must meet tol itself. In mixed precision a
-    truncation decision can also flip: FP32 and FP64 singular values that
-    straddle the tie gap or the cutoff tail are cut differently, and the states
-    then part by one group's weight. Such a sample is reported; at most half of
-    the samples may flip, and estimator bias is tested separately."""
+def _compare_truncated(T, ctx, prob, par, tol, init=None, mixed_all_determined=True):
+    """Truncated runs, compared per (sample, snapshot). Truncation makes the
+    evolution a nonlinear map that can amplify rounding: the oracle itself,
+    rerun in another exact gauge (centre moved back after every update), may
+    then part from its first run. d = |oracle - oracle in the other gauge|.
+      - Where the oracle reproduces itself (d <= tol / 10), the GPU value must
+        lie within tol of it.
+      - Where it does not, FP64 arithmetic does not fix the value to tol in any
+        implementation; there the GPU must agree with the oracle as well as the
+        oracle agrees with itself: |gpu - oracle| <= 4 d. Mixed-precision cases
+        are chosen so that every value is fixed, and that is asserted.
+    Returns (gpu, oracle, number of values held to tol)."""
     got = T.tepai_sample_values(ctx, prob, par, init)
-    floor_rel, gap_rel = (1e-14, 1e-4) if par.precision == 0 else (4e-6, 1e-4)
-    kw = dict(init_tensors=None if init is None else init[0], floor_rel=floor_rel, gap_rel=gap_rel)
+    kw = dict(init_tensors=None if init is None else init[0], **oracle_rule(par))
     ref = oracle_run.run(prob, par, **kw)
     alt = oracle_run.run(prob, par, regauge=True, **kw)
     assert np.array_equal(got["sign"], ref["sign"])
-    scale = 10.0 if par.precision == 0 else 1e10
-    report, strict, flips = [], 0, 0
-    for si in range(par.n_samples):
-        err = float(np.max(np.abs(got["v"][si] - ref["v"][si])))
-        d_s = float(np.max(np.abs(alt["v"][si] - ref["v"][si])))
-        report.append((si, err, d_s))
-        bound = max(tol, scale * d_s)
-        if par.precision == 1 and err > bound:
-            # a truncation decision (tie at the 1e-4 gap, cutoff tail) taken
-            # differently by FP32 and FP64 keys: the states part by the weight of
-            # one singular-value group
-            flips += 1
-        else:
-            assert err <= bound, (si, err, d_s)
-        strict += err <= tol
-    print("per sample (index, |gpu - oracle|, oracle gauge spread):", report, "flips:", flips)
-    assert 2 * strict >= par.n_samples, report
-    assert 2 * flips <= par.n_samples, report
-    return got, ref
+    err = np.max(np.abs(got["v"] - ref["v"]), axis=2)          # (samples, snapshots)
+    d = np.max(np.abs(alt["v"] - ref["v"]), axis=2)
+    fixed = d <= tol / 10
+    if par.precision == 1 and mixed_all_determined:
+        assert np.all(fixed), d
+    print("values held to tol:", int(fixed.sum()), "of", fixed.size,
+          "| worst held:", float(err[fixed].max(initial=0.0)),
+          "| not fixed by FP64 (err, d):", list(zip(err[~fixed].round(12), d[~fixed].round(12))))
+    assert np.all(err[fixed] <= tol), err
+    assert np.all(err[~fixed] <= 4 * d[~fixed]), (err, d)
+    return got, ref, int(fixed.sum())
 
 
-def test_fp64_truncated_matches_oracle(T, ctx):
+@pytest.mark.parametrize("tie", [0.0, 1e-4])
+def test_fp64_truncated_matches_oracle(T, ctx, tie):
+    """chi = 6 on a ring of 10, ~400 steps: the paper's tie rule and the 1e-4
+    band, both taken by the oracle and the kernel."""
     prob = W.spin_ring(10, 1.0, seed=3)
-    par = P(n_samples=4, chi_max=6, cutoff=1e-9, T=1.0, n_steps=400, delta=math.pi / 32)
-    got, ref = _compare_truncated(T, ctx, prob, par, TOL64)
+    par = P(n_samples=8, chi_max=6, cutoff=1e-9, T=1.0, n_steps=400, delta=math.pi / 32, tie_rel=tie)
+    got, ref, held = _compare_truncated(T, ctx, prob, par, TOL64)
     assert max(s["max_chi"] for s in ref["stats"]) == 6
+    assert held >= 24
 
 
 def test_fp64_from_random_mps_matches_oracle(T, ctx):
@@ -170,34 +165,66 @@ def test_no_pi_variant_fp64(T, ctx):
 
 
 # ------------------------------------------------------------------ mixed precision
-def test_mixed_truncated_matches_oracle(T, ctx):
-    """Heavy truncation (chi = 16 on a ring of 12), short horizon (~600
-    updates per sample): per-sample parity at 1e-4, decision flips reported."""
+@pytest.mark.parametrize("tie", [0.0, 1e-4])
+def test_mixed_truncated_matches_oracle(T, ctx, tie):
+    """Heavy truncation (chi = 16 on a ring of 12), ~600 updates per sample, 32
+    samples: every value within 1e-4 of the oracle, under the paper's tie rule
+    and under the 1e-4 band."""
     prob = W.spin_ring(12, 2.0, seed=0)
-    par = P(n_samples=8, chi_max=16, cutoff=1e-10, T=0.125, n_steps=48, delta=math.pi / 64,
-            precision=1)
+    par = P(n_samples=32, chi_max=16, cutoff=1e-10, T=0.125, n_steps=48, delta=math.pi / 64,
+            precision=1, tie_rel=tie)
     _compare_truncated(T, ctx, prob, par, TOLMIX)
 
 
-def test_mixed_precision_does_not_bias_the_estimator(T, ctx):
-    """Long heavily truncated runs: FP32 and FP64 singular values occasionally
-    cut a nearly tied group differently, and a sample then departs by that
-    group's weight. The estimator must not be biased by it: per observable and
-    snapshot, the mean of sign * (v_mixed - v_fp64) over 96 samples lies within
-    4 standard errors of zero. The FP64 run is the oracle-checked path."""
-    prob = W.spin_ring(12, 2.0, seed=0)
-    p64 = P(n_samples=96, chi_max=16, cutoff=1e-10, T=1.0, n_steps=400, delta=math.pi / 64,
-            n_snapshots=2, precision=0)
-    pmx = W.Params(**{**p64.__dict__, "precision": 1})
-    a = T.tepai_sample_values(ctx, prob, p64)
-    b = T.tepai_sample_values(ctx, prob, pmx)
-    assert np.array_equal(a["sign"], b["sign"])
-    d = a["sign"][:, :, None] * (b["v"] - a["v"])
-    mean = d.mean(axis=0)
-    se = d.std(axis=0, ddof=1) / math.sqrt(d.shape[0])
-    assert np.all(np.abs(mean) <= 4 * se + 1e-4), (np.abs(mean).max(), se.max())
-    flips = int(np.sum(np.max(np.abs(d), axis=(1, 2)) > 1e-3))
-    print("samples departing by > 1e-3:", flips, "of", d.shape[0])
+def _sv_chunk(args):
+    """State-vector oracle values of samples [lo, hi) of ring8_heisenberg_T1
+    (worker of a spawned process pool)."""
+    lo, hi = args
+    import workloads as Wk
+    from oracle import run as orun
+    prob, par, _ = Wk.workload(Wk.RING8)
+    r = orun.run(prob, par, use_statevector=True, samples=range(lo, hi))
+    return r["v"], r["sign"]
+
+
+def test_ring8_ensemble_matches_statevector_oracle(T, ctx):
+    """ring8_heisenberg_T1, all 1000 circuits (about 4700 events each; chi = 16
+    is exact on 8 sites): the FP64 and the mixed-precision ensemble means of
+    <Z_0> at the 10 snapshots against the exact state-vector oracle on the same
+    circuits, per snapshot: FP64 within 1e-10, mixed within 1e-4. The
+    per-snapshot errors and per-sample error quantiles are printed."""
+    import multiprocessing as mp
+    from oracle import estimator
+    prob, par, _ = W.workload(W.RING8)
+    chunks = [(lo, min(lo + 25, par.n_samples)) for lo in range(0, par.n_samples, 25)]
+    # one BLAS thread per worker process: the state-vector steps are tiny
+    # matrix products, and per-process BLAS thread pools would oversubscribe
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            res = pool.map(_sv_chunk, chunks)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    v_ref = np.concatenate([r[0] for r in res])
+    s_ref = np.concatenate([r[1] for r in res])
+    g, _ = T.tepai_gnorm(prob, par)
+    mean_ref, se_ref, _ = estimator.estimate(v_ref, s_ref, g)
+    for prec, tol in ((0, TOL64), (1, TOLMIX)):
+        got = T.tepai_sample_values(ctx, prob, W.Params(**{**par.__dict__, "precision": prec}))
+        assert np.array_equal(got["sign"], s_ref)
+        mean, _, _ = estimator.estimate(got["v"], got["sign"], g)
+        per_snap = np.abs(mean - mean_ref)[:, 0]
+        per_sample = np.max(np.abs(got["v"] - v_ref), axis=(1, 2))
+        print("precision", prec, "| ensemble error per snapshot:", per_snap,
+              "| per-sample quantiles (50, 90, 99, 100%):", np.quantile(per_sample, [0.5, 0.9, 0.99, 1.0]),
+              "| stderr:", float(se_ref.max()), "| reorth SVDs:", got["stats"]["jacobi_reorth"])
+        assert per_snap.max() <= tol, per_snap
 
 
 def test_mixed_weakly_truncated_matches_oracle(T, ctx):
@@ -216,6 +243,36 @@ def test_mixed_ring8_matches_statevector(T, ctx):
     prob, par, _ = W.workload(W.RING8)
     par = W.Params(**{**par.__dict__, "n_samples": 2, "precision": 1, "obs_sites": None})
     _compare(T, ctx, prob, par, TOLMIX, use_sv=True)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMIX)])
+def test_negative_and_zero_couplings(T, ctx, precision, tol):
+    """Bond terms with c_k < 0 (B = R(sign(theta) Delta)) and c_k = 0 (q_k = 0:
+    the term never fires), mixed with positive ones, on a ring of 8 and an open
+    chain of 7, against the oracle."""
+    for n, periodic in ((8, True), (7, False)):
+        prob = W.spin_ring(n, 1.0, seed=11, periodic=periodic)
+        nb = prob.n_bonds
+        prob.Jx = np.array([(-1.0) ** b * (0.5 + 0.25 * b) for b in range(nb)])
+        prob.Jy = np.array([0.0 if b % 3 == 0 else -0.8 for b in range(nb)])
+        prob.Jz = np.array([-0.5 if b % 2 else 0.0 for b in range(nb)])
+        par = P(n_samples=6, chi_max=16, cutoff=1e-12, T=0.6, n_steps=240, delta=math.pi / 32,
+                precision=precision)
+        got, ref, err = _compare(T, ctx, prob, par, tol)
+        assert np.any(got["sign"] == -1)
+
+
+def test_fp64_chi128_staged_paths(T, ctx):
+    """FP64 at chi = 128 (theta' 256 x 256: blocked Householder on 256 rows, the
+    staged Jacobi with 8 rows per lane, one 512-thread CTA per SM) on a ring of
+    16 from a random MPS at the cap, two samples, one Trotter step."""
+    prob = W.spin_ring(16, 1.0, seed=5, Jz=0.5)
+    tens, dims = W.random_mps_tensors(16, 128, seed=105)
+    par = W.Params(T=3.0, n_steps=18000, delta=math.pi / 1024, n_samples=2, chi_max=128,
+                   cutoff=1e-10, n_snapshots=1, seed=7, precision=0, run_steps=1)
+    got, ref, err = _compare(T, ctx, prob, par, TOL64, init=(tens, dims))
+    assert max(s["max_chi"] for s in ref["stats"]) == 128
+    assert got["stats"]["gate_updates"] + got["stats"]["swap_updates"] > 0
 
 
 # ------------------------------------------------------------------ estimator
@@ -253,8 +310,8 @@ def test_results_independent_of_grid(T, ctx):
 # ------------------------------------------------------------------ full-size bench workload
 def test_bench_workload_sampled_parity(T):
     """The launch bench.py times (chi = 128, n = 64, 16 samples per SM, one Trotter
-    step, default launch shape, shared random MPS at the cap): sampled samples of
-    the batch against the oracle, one by one."""
+    step, default launch shape, shared random MPS at the cap): six samples spread
+    over the queue against the oracle, one by one."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     batch = 16 * sms
@@ -269,8 +326,8 @@ def test_bench_workload_sampled_parity(T):
     assert st["max_chi"] == 128
     v = v.cpu().numpy()
     sg = sg.cpu().numpy()
-    for si in (0, batch - 1):
-        ref = oracle_run.run(prob, par, init_tensors=init[0], floor_rel=4e-6, gap_rel=1e-4,
+    for si in sorted({0, batch // 5, 2 * batch // 5, 3 * batch // 5, 4 * batch // 5, batch - 1}):
+        ref = oracle_run.run(prob, par, init_tensors=init[0], **oracle_rule(par),
                              samples=[777 + si])
         err = float(np.max(np.abs(v[si] - ref["v"][0])))
         assert err <= TOLMIX, (si, err)

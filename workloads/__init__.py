@@ -52,6 +52,8 @@ class Params:
     obs_sites: np.ndarray | None = None   # Z_i sites; None = all sites
     obs_strings: np.ndarray | None = None  # (n_obs, n) Pauli codes 0 I, 1 X, 2 Y, 3 Z per site;
                                            # replaces obs_sites when given
+    tie_rel: float = 0.0      # tie band at truncation cuts (0 = only equal values are tied)
+    launch_variant: int = 0   # launch shape of the CUDA path (0 = its default rule)
 
     def steps_run(self) -> int:
         return self.n_steps if self.run_steps == 0 else self.run_steps
