@@ -5,15 +5,49 @@
 
 namespace tepai {
 
+// Reflector of column y at row j (rows j..m-1, warp-collective; lane 0 writes
+// vhead[j], tau[j] and alpha[j]). Squares, sums, |x_0| and the phase
+// x_0 / |x_0| are taken in FP64 whatever R is: the square of an FP32 entry
+// below about 1e-19 falls into the subnormal range and keeps only a few
+// significant bits, and a norm or phase taken from it would make
+// I - tau v v^H non-unitary (tau |v|^2 != 2), so that a Q formed from it is no
+// longer an isometry. In FP64 the squares of FP32 values are always exact
+// enough. The reflector is skipped (tau = 0, H = I) when the column's |x|^2 is
+// at most tiny2 or tau does not fit R.
+template <typename R>
+__device__ __forceinline__ void householder_reflector(const cplx<R>* y, int j, int m, int lane, double tiny2,
+                                                      cplx<R>* vhead, cplx<R>* tau, cplx<R>* alpha) {
+  double nr2 = 0.0;
+  for (int row = j + lane; row < m; row += 32) {
+    const double re = (double)y[row].re, im = (double)y[row].im;
+    nr2 = fma(re, re, fma(im, im, nr2));
+  }
+  nr2 = warp_sum(nr2);
+  if (lane != 0) return;
+  const cplx<R> x0 = y[j];
+  const double xr = (double)x0.re, xi = (double)x0.im;
+  const double ax0 = sqrt(fma(xr, xr, xi * xi));
+  const double nrm = sqrt(nr2);
+  const double tj = 1.0 / (nrm * (nrm + ax0));
+  if (!(nr2 > tiny2) || !(nrm > 0.0) || !isfinite((R)tj)) {
+    vhead[j] = cplx<R>{1, 0}; tau[j] = cplx<R>{0, 0}; alpha[j] = x0;
+    return;
+  }
+  const double pr = ax0 > 0.0 ? xr / ax0 : 1.0, pi = ax0 > 0.0 ? xi / ax0 : 0.0;
+  alpha[j] = cplx<R>{(R)(-pr * nrm), (R)(-pi * nrm)};
+  vhead[j] = cplx<R>{(R)(pr * (ax0 + nrm)), (R)(pi * (ax0 + nrm))};
+  tau[j] = cplx<R>{(R)tj, 0};
+}
+
 // Householder QR of Y (m x nq, column-major, ld m): Y = Q R with r = min(m, nq).
 // Reflector j is H_j = I - tau_j v_j v_j^H, v_j = (vhead_j, Y[j+1.., j]); it maps
 // the column onto alpha_j e_j with alpha_j = -e^{i arg x_0} |x|. On return the
 // strict upper triangle of R is in Y, its diagonal in alpha[], and Q (m x r,
 // column-major) is formed explicitly by backward accumulation unless Q is null.
 // A reflector is skipped (tau = 0) when the remaining column has |x|^2 <= tiny2,
-// or when tau = 1/(|x|(|x|+|x_0|)) is not finite: an evolved state carries
-// amplitudes like sin(Delta/2)^k whose squares underflow FP32, and the scale
-// would overflow.
+// or when tau = 1/(|x|(|x|+|x_0|)) does not fit R: an evolved state carries
+// amplitudes like sin(Delta/2)^k far below 1e-19, and the scale would
+// overflow FP32 (householder_reflector takes the norms themselves in FP64).
 template <typename R>
 __device__ __noinline__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, double tiny2) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
@@ -24,26 +58,7 @@ __device__ __noinline__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, d
   {
   SubTimer spt(st, SP_QR_PANEL);
   for (int j = 0; j < r; ++j) {
-    if (w == 0) {
-      const C* y = Y + (size_t)j * m;
-      R nr2 = 0;
-      for (int row = j + lane; row < m; row += 32) nr2 += abs2(y[row]);
-      nr2 = warp_sum(nr2);
-      if (lane == 0) {
-        const C x0 = y[j];
-        const R ax0 = sqrt(abs2(x0));
-        const R nrm = sqrt(nr2);
-        const R tj = R(1) / (nrm * (nrm + ax0));
-        if (!((double)nr2 > tiny2) || !(nrm > R(0)) || !isfinite(tj)) {
-          vhead[j] = C{1, 0}; tau[j] = C{0, 0}; alpha[j] = x0;
-        } else {
-          const C ph = ax0 > R(0) ? C{x0.re / ax0, x0.im / ax0} : C{1, 0};
-          alpha[j] = C{-ph.re * nrm, -ph.im * nrm};
-          vhead[j] = C{ph.re * (ax0 + nrm), ph.im * (ax0 + nrm)};
-          tau[j] = C{tj, 0};
-        }
-      }
-    }
+    if (w == 0) householder_reflector<R>(Y + (size_t)j * m, j, m, lane, tiny2, vhead, tau, alpha);
     __syncthreads();
     const C vh = vhead[j];
     const R tj = tau[j].re;
@@ -511,26 +526,7 @@ __device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq,
     if (failed()) return;
     for (int jj = 0; jj < bp; ++jj) {
       const int j = j0 + jj;
-      if (w == 0) {
-        const C* y = P + (size_t)jj * m;
-        R nr2 = 0;
-        for (int row = j + lane; row < m; row += 32) nr2 += abs2(y[row]);
-        nr2 = warp_sum(nr2);
-        if (lane == 0) {
-          const C x0 = y[j];
-          const R ax0 = sqrt(abs2(x0));
-          const R nrm = sqrt(nr2);
-          const R tj = R(1) / (nrm * (nrm + ax0));
-          if (!((double)nr2 > tiny2) || !(nrm > R(0)) || !isfinite(tj)) {
-            vhead[j] = C{1, 0}; tau[j] = C{0, 0}; alpha[j] = x0;
-          } else {
-            const C ph = ax0 > R(0) ? C{x0.re / ax0, x0.im / ax0} : C{1, 0};
-            alpha[j] = C{-ph.re * nrm, -ph.im * nrm};
-            vhead[j] = C{ph.re * (ax0 + nrm), ph.im * (ax0 + nrm)};
-            tau[j] = C{tj, 0};
-          }
-        }
-      }
+      if (w == 0) householder_reflector<R>(P + (size_t)jj * m, j, m, lane, tiny2, vhead, tau, alpha);
       __syncthreads();
       const C vh = vhead[j];
       const R tj = tau[j].re;

@@ -82,9 +82,23 @@ __device__ __forceinline__ bool rot_params(R al, R be, R gr, R gi, R tol, R thr,
     // warp sums and the rotation holds no division and no square root. The
     // phase has unit modulus and c^2 + s^2 = 1 to rsqrt accuracy (a few ulp).
     // A zero or non-finite g gives NaN in the test and no rotation.
-    const float h = fmaf(gr, gr, gi * gi);
-    const float ig = rsqrtf(h);
-    const float cosv = (h * ig) * (rsqrtf(al) * rsqrtf(be));
+    // Below |g| ~ 1e-15 the squares approach the subnormal range, where they
+    // keep few significant bits and the phase g / |g| would lose unit modulus
+    // (a non-unitary rotation); g is then scaled by 2^60 before squaring.
+    float h = fmaf(gr, gr, gi * gi);
+    float ig, ag;
+    if (h >= 1.0e-30f) {
+      ig = rsqrtf(h);
+      ag = h * ig;
+    } else {
+      const float S = 1152921504606846976.0f;  // 2^60
+      const float grs = gr * S, gis = gi * S;
+      h = fmaf(grs, grs, gis * gis);
+      const float igs = rsqrtf(h);
+      ig = igs * S;
+      ag = (h * igs) * (1.0f / S);
+    }
+    const float cosv = ag * (rsqrtf(al) * rsqrtf(be));
     if (!(cosv > tol)) return false;
     const float zeta = 0.5f * (be - al) * ig;
     const float az = fabsf(zeta);

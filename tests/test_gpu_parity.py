@@ -265,11 +265,13 @@ def test_negative_and_zero_couplings(T, ctx, precision, tol):
 def test_fp64_chi128_staged_paths(T, ctx):
     """FP64 at chi = 128 (theta' 256 x 256: blocked Householder on 256 rows, the
     staged Jacobi with 8 rows per lane, one 512-thread CTA per SM) on a ring of
-    16 from a random MPS at the cap, two samples, one Trotter step."""
+    16 from a random MPS at the cap, two samples, one Trotter step. With no
+    weight cutoff the kept bond reaches the cap (a cutoff of 1e-10 would stop
+    this random spectrum at 119)."""
     prob = W.spin_ring(16, 1.0, seed=5, Jz=0.5)
     tens, dims = W.random_mps_tensors(16, 128, seed=105)
     par = W.Params(T=3.0, n_steps=18000, delta=math.pi / 1024, n_samples=2, chi_max=128,
-                   cutoff=1e-10, n_snapshots=1, seed=7, precision=0, run_steps=1)
+                   cutoff=0.0, n_snapshots=1, seed=7, precision=0, run_steps=1)
     got, ref, err = _compare(T, ctx, prob, par, TOL64, init=(tens, dims))
     assert max(s["max_chi"] for s in ref["stats"]) == 128
     assert got["stats"]["gate_updates"] + got["stats"]["swap_updates"] > 0
