@@ -100,10 +100,12 @@ typedef struct {
     int launch_variant;            /* 0 = built-in launch-shape rule. When the SVD working matrix is
                                       staged from global memory: 1 = two 256-thread CTAs per SM,
                                       2 = one 512-thread CTA per SM (both with the CUDA-core Jacobi
-                                      passes), 7 = two 256-thread CTAs per SM running the Jacobi's
-                                      Gram matrices and block updates on the tensor cores (TF32
-                                      operands split in two, FP32 accumulation; TEPAI_MIXED with
-                                      chi_max <= 128, the default there). When it fits in shared
+                                      passes), 7 = 256-thread CTAs running the Jacobi's Gram
+                                      matrices and block updates and the theta and projection
+                                      products on the tensor cores (TF32 operands split in two,
+                                      FP32 accumulation; TEPAI_MIXED with chi_max <= 128; one CTA
+                                      per SM, as for any kernel holding tensor memory, so only on
+                                      request). When it fits in shared
                                       memory: 3, 4, 5, 6 = 64, 128, 256, 512 threads per CTA
                                       (smaller CTAs run more samples per SM). Variants that do not
                                       apply are ignored. tepai_autotune reports the fastest on this

@@ -12,15 +12,15 @@ namespace tepai {
 cudaError_t launch_ensemble_f32(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_ensemble_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_canon_f32(const KArgs& a, int block, size_t smem, cudaStream_t st);
-const void* ensemble_kernel_fn_f32();
+const void* ensemble_kernel_fn_f32(int use_tc);
 cudaError_t launch_ensemble_captured_f32(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_ensemble_captured_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
-const void* ensemble_kernel_fn_f64();
-cudaError_t set_ensemble_smem_f32(size_t smem);
-cudaError_t set_ensemble_smem_f64(size_t smem);
+const void* ensemble_kernel_fn_f64(int use_tc);
+cudaError_t set_ensemble_smem_f32(size_t smem, int use_tc);
+cudaError_t set_ensemble_smem_f64(size_t smem, int use_tc);
 cudaError_t launch_canon_f64(const KArgs& a, int block, size_t smem, cudaStream_t st);
-cudaError_t occupancy_ensemble_f32(int block, size_t smem, int* ctas_per_sm);
-cudaError_t occupancy_ensemble_f64(int block, size_t smem, int* ctas_per_sm);
+cudaError_t occupancy_ensemble_f32(int block, size_t smem, int use_tc, int* ctas_per_sm);
+cudaError_t occupancy_ensemble_f64(int block, size_t smem, int use_tc, int* ctas_per_sm);
 cudaError_t launch_signed_reduce(const double* v, const signed char* sign, long long ns, int M, int nobs,
                                  const double* gnorm, double* mean, double* se, double* part, cudaStream_t st);
 cudaError_t launch_export_circuit(const KArgs& a, unsigned long long s, int* buf, long long cap,
@@ -170,9 +170,9 @@ int launch_shape(const HostPlan& hp, const tepai_params* Q, int grid_req, Launch
   int sms = 0, optin = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  auto occ = [&](int block, size_t smem, int* per_sm) {
-    return Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(block, smem, per_sm)
-                                      : occupancy_ensemble_f32(block, smem, per_sm);
+  auto occ = [&](int block, size_t smem, int use_tc, int* per_sm) {
+    return Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(block, smem, use_tc, per_sm)
+                                      : occupancy_ensemble_f32(block, smem, use_tc, per_sm);
   };
   CK(choose_launch_shape(hp.n, hp.L, Q->variant == TEPAI_CONTINUOUS ? hp.L : 0, Q->chi_max, nc.csize, optin, occ, ls, Q->launch_variant));
   ls.grid = grid_req > 0 ? grid_req : sms * ls.per_sm;
@@ -309,7 +309,8 @@ cudaError_t capture_execute(Prepared& pr, double* d_mean, double* d_se, double* 
                             signed char* d_sign, cudaStream_t st) {
   graph_free(pr.g);
   // the launch sets the kernel's shared-memory attribute; do it outside the capture
-  cudaError_t e = pr.precision == TEPAI_FP64 ? set_ensemble_smem_f64(pr.smem) : set_ensemble_smem_f32(pr.smem);
+  cudaError_t e = pr.precision == TEPAI_FP64 ? set_ensemble_smem_f64(pr.smem, pr.ka.use_tc)
+                                             : set_ensemble_smem_f32(pr.smem, pr.ka.use_tc);
   if (e != cudaSuccess) return e;
   cudaStream_t cs = st;
   if (is_default_stream(st)) {
@@ -324,7 +325,7 @@ cudaError_t capture_execute(Prepared& pr, double* d_mean, double* d_se, double* 
   e = cudaStreamEndCapture(cs, &graph);
   if (eq != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return eq; }
   if (e != cudaSuccess) return e;
-  const void* fn = pr.precision == TEPAI_FP64 ? ensemble_kernel_fn_f64() : ensemble_kernel_fn_f32();
+  const void* fn = pr.precision == TEPAI_FP64 ? ensemble_kernel_fn_f64(pr.ka.use_tc) : ensemble_kernel_fn_f32(pr.ka.use_tc);
   size_t nn = 0;
   if ((e = cudaGraphGetNodes(graph, nullptr, &nn)) != cudaSuccess) { cudaGraphDestroy(graph); return e; }
   std::vector<cudaGraphNode_t> nodes(nn);

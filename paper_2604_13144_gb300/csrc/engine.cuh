@@ -226,9 +226,14 @@ struct SmemLayout {
   void* x;            // SVD working matrix (optional)
 };
 
-template <typename R>
+// TC = true: the engine of the kernel that may hold TMEM, whose single-precision
+// SVDs and products can run on the tensor cores. With TC = false no tcgen05
+// code is compiled into the engine at all: a kernel that contains any
+// tcgen05 instruction is limited to one CTA per SM.
+template <typename R, bool TC = false>
 struct Engine {
   using C = cplx<R>;
+  static constexpr bool kTC = TC && sizeof(R) == 4;
   const KArgs& a;
   SmemLayout sm;
   C* site0;
@@ -390,7 +395,7 @@ struct Engine {
   // a complex product goes to the tensor cores when the CTA holds TMEM and the
   // product is large enough to fill 128-row tiles (below that, block_gemm)
   __device__ bool tc_worth(int M, int N, int K) const {
-    return sizeof(R) == 4 && tc_ok && (long long)M * N * K >= 64LL * 64 * 64;
+    return kTC && tc_ok && (long long)M * N * K >= 64LL * 64 * 64;
   }
   __device__ bool tc_wait(int s);
   __device__ void reorth_pass_f64(C* X, int m, int nc, bool x_in_smem, double thr);

@@ -9,8 +9,8 @@
 
 namespace tepai {
 
-template <typename R>
-__device__ __noinline__ void Engine<R>::init_product() {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::init_product() {
   for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = 1;
   // single-site codes 0 |0>, 1 |1>, 2 |+>, 3 |->, 4 |+i>, 5 |-i>
   const R r = (R)0.70710678118654752440;
@@ -34,8 +34,8 @@ __device__ __noinline__ void Engine<R>::init_product() {
 // centre is rescaled to unit norm after every step of the sweep: the norm of an
 // unnormalised input grows geometrically along the chain and would overflow
 // FP32 long before site 0.
-template <typename R>
-__device__ __noinline__ void Engine<R>::init_from_tensors() {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::init_from_tensors() {
   for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = a.init_dims[i];
   __syncthreads();
   for (int i = 0; i <= a.n; ++i)
@@ -61,8 +61,8 @@ __device__ __noinline__ void Engine<R>::init_from_tensors() {
 // dimensions, centre and site tensors are copied (16-byte vectors; every site
 // slot starts 16-byte aligned and holds a multiple of 16 bytes when the
 // dimensions are even, else the tail is copied element-wise).
-template <typename R>
-__device__ __noinline__ void Engine<R>::init_from_canonical() {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::init_from_canonical() {
   for (int i = tid(); i <= a.n; i += nt()) sm.dims[i] = a.canon_meta[i];
   __syncthreads();
   for (int i = 0; i <= a.n; ++i)
@@ -87,8 +87,8 @@ __device__ __noinline__ void Engine<R>::init_from_canonical() {
 // Write the MPS (any gauge; normalised) to out in the start-state layout:
 // site tensors A_p[d_p][2][d_{p+1}] concatenated over chain positions, complex
 // interleaved in FP64; bond dimensions to dims[0..n].
-template <typename R>
-__device__ __noinline__ void Engine<R>::export_state(double* out, int* dims) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::export_state(double* out, int* dims) {
   for (int i = tid(); i <= a.n; i += nt()) dims[i] = sm.dims[i];
   size_t off = 0;
   for (int i = 0; i < a.n; ++i) {
@@ -105,8 +105,8 @@ __device__ __noinline__ void Engine<R>::export_state(double* out, int* dims) {
 }
 
 // Rescale the centre tensor (and so the state) to unit norm.
-template <typename R>
-__device__ __noinline__ void Engine<R>::normalise_centre() {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::normalise_centre() {
   if (failed()) return;
   const int c = centre;
   const int cnt = sm.dims[c] * 2 * sm.dims[c + 1];
@@ -120,8 +120,8 @@ __device__ __noinline__ void Engine<R>::normalise_centre() {
   __syncthreads();
 }
 
-template <typename R>
-__device__ __noinline__ void Engine<R>::apply_1site(int i, const C u[4]) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::apply_1site(int i, const C u[4]) {
   PhaseTimer pt(st, PH_SINGLE);
   const int dl = sm.dims[i], dr = sm.dims[i + 1];
   C* p = S(i);
@@ -151,8 +151,8 @@ template <typename R> __device__ __forceinline__ void pauli2(int p, cplx<R> u[4]
 // n-2, ..., so a bond term joins positions one or two apart. A gate two apart
 // swaps the far site next to the near one, acts, and swaps it back; every swap
 // is a truncated two-site update.
-template <typename R>
-__device__ __noinline__ void Engine<R>::apply_event(int k, int v, int& sign_count) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::apply_event(int k, int v, int& sign_count) {
   if (failed()) return;
   const TermDev& T = a.terms[k];
   if (tid() == 0) st.events++;
@@ -190,8 +190,8 @@ __device__ __noinline__ void Engine<R>::apply_event(int k, int v, int& sign_coun
 // transfer-matrix sweep rightward from c (E <- sum_s A^s^H E A^s) gives
 // <Z_i> for i >= c and a sweep leftward from c (F <- sum_s A^s F A^s^H) gives
 // <Z_i> for i < c.
-template <typename R>
-__device__ __noinline__ void Engine<R>::measure_z(double* zout) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::measure_z(double* zout) {
   if (failed()) return;
   PhaseTimer pt(st, PH_MEASURE);
   const int n = a.n, c = centre;
@@ -347,8 +347,8 @@ __device__ __noinline__ void Engine<R>::measure_z(double* zout) {
 //   T^t[a][d] = sum_b E[a][b] A[b][t][d],  U^s = sum_t O[s][t] T^t,
 //   E'[c][d]  = sum_{a,s} conj(A[a][s][c]) U^s[a][d],
 // and <P> = Tr E at bond hi + 1, divided by |centre|^2.
-template <typename R>
-__device__ __noinline__ void Engine<R>::measure_strings(double* out) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::measure_strings(double* out) {
   if (failed()) return;
   PhaseTimer pt(st, PH_MEASURE);
   const int n = a.n, c = centre;
@@ -530,8 +530,8 @@ __host__ __device__ inline SmemLayout carve_smem(unsigned char* base, const KArg
 
 // One sample of the N -> infinity sampler: the events of all terms merged in
 // time order; snapshot m is taken once the next event lies beyond t_m.
-template <typename R>
-__device__ __noinline__ void run_continuous(Engine<R>& eng, const KArgs& a, const SmemLayout& sm, long long si,
+template <typename R, bool TC>
+__device__ __noinline__ void run_continuous(Engine<R, TC>& eng, const KArgs& a, const SmemLayout& sm, long long si,
                                             unsigned long long s) {
   int sign_count = 0;
   int mi = 0;
@@ -568,7 +568,10 @@ __device__ __noinline__ void run_continuous(Engine<R>& eng, const KArgs& a, cons
   }
 }
 
-template <typename R>
+// TC selects the instantiation that may hold TMEM (single precision, the
+// tensor-core launch shape). The instantiation without it contains no TMEM
+// allocation, which the occupancy of the CUDA-core launch shapes depends on.
+template <typename R, bool TC>
 __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant__ KArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_next;
@@ -576,11 +579,14 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
   __shared__ __align__(8) unsigned long long s_tcbar[2];
   SmemLayout sm = carve_smem(smem_raw, a, (int)sizeof(cplx<R>));
   char* arena = a.arena + (size_t)blockIdx.x * a.arena_stride;
-  Engine<R> eng(a, sm, arena);
+  Engine<R, TC> eng(a, sm, arena);
   // single precision with the tensor-core launch shape: hold TMEM for the
   // whole kernel (one warp allocates and, at the end, frees it)
-  const bool use_tc = sizeof(R) == 4 && a.use_tc && blockDim.x >= 128;
-  if (use_tc && threadIdx.x < 32) { tc::alloc(&s_tmem, TcJac::TMEM_COLS); tc::relinquish(); }
+  bool use_tc = false;
+  if constexpr (TC && sizeof(R) == 4) use_tc = a.use_tc && blockDim.x >= 128;
+  if constexpr (TC && sizeof(R) == 4) {
+    if (use_tc && threadIdx.x < 32) { tc::alloc(&s_tmem, TcJac::TMEM_COLS); tc::relinquish(); }
+  }
   if (threadIdx.x == 0) {
     sm.ibuf[13] = 0; sm.ibuf[14] = 0; sm.ibuf[15] = 0;
     sm.ibuf[7] = a.wait_limit > 0 ? a.wait_limit : (1 << 22);
@@ -666,18 +672,20 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
     atomicAdd(&a.stats->reorth, st.reorth);
     atomicAdd(&a.stats->tc_flops, st.tc_flops);
   }
-  if (use_tc) {
-    // no MMA may still be writing TMEM when it is freed: bounded waits for the
-    // latest commit on each stage barrier (already complete unless a wait
-    // timed out), then the allocating warp frees the columns
-    for (int s = 0; s < 2; ++s) {
-      if (eng.tc_cnt[s] == 0) continue;
-      bool ok = false;
-      for (int it = 0; it < (1 << 24) && !ok; ++it) ok = bulk::try_wait(s_tcbar + s, (eng.tc_cnt[s] - 1) & 1u);
+  if constexpr (TC && sizeof(R) == 4) {
+    if (use_tc) {
+      // no MMA may still be writing TMEM when it is freed: bounded waits for
+      // the latest commit on each stage barrier (already complete unless a
+      // wait timed out), then the allocating warp frees the columns
+      for (int s = 0; s < 2; ++s) {
+        if (eng.tc_cnt[s] == 0) continue;
+        bool ok = false;
+        for (int it = 0; it < (1 << 24) && !ok; ++it) ok = bulk::try_wait(s_tcbar + s, (eng.tc_cnt[s] - 1) & 1u);
+      }
+      tc::fence_before();
+      __syncthreads();
+      if (threadIdx.x < 32) tc::dealloc(eng.tmem, TcJac::TMEM_COLS);
     }
-    tc::fence_before();
-    __syncthreads();
-    if (threadIdx.x < 32) tc::dealloc(eng.tmem, TcJac::TMEM_COLS);
   }
 }
 

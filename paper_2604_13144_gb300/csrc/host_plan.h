@@ -294,10 +294,7 @@ struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems, per_s
 // reports resident CTAs per SM of a (block, smem) pair. When the whole SVD
 // working matrix (2cap x 2cap) fits in shared memory it stays there; otherwise
 // it lives in global memory and column blocks are staged.
-//   - Single precision with at most 256 rows (cap <= 128): 256-thread CTAs,
-//     two per SM, whose staging room holds the tensor-core Jacobi's operand
-//     stage, Gram matrix and rotation (TcJac::BYTES); each CTA holds TMEM.
-//   - Otherwise staged shapes first try two samples per SM (256 threads each,
+//   - Staged shapes first try two samples per SM (256 threads each,
 //     staging room for a 16-column Householder panel and one 16-column update
 //     chunk, which also holds two 16-column Jacobi blocks): two independent
 //     CTAs fill each other's barrier, latency and copy-wait stalls, and the
@@ -305,7 +302,11 @@ struct LaunchShape { int grid, block; size_t smem; int x_in_smem, x_elems, per_s
 //     fit, one 512-thread CTA per SM stages blocks within 128 KB.
 // `variant` forces a shape. For a staged working matrix: 1 = two 256-thread
 // CTAs per SM, 2 = one 512-thread CTA per SM (both with the CUDA-core Jacobi
-// passes), 7 = the tensor-core shape. When the working matrix fits in shared
+// passes), 7 = the tensor-core shape (single precision, at most 256 rows:
+// 256-thread CTAs whose staging room holds the tensor-core Jacobi's operand
+// stage, Gram matrix and rotation, TcJac::BYTES; each CTA holds TMEM, and a
+// kernel with tcgen05 code runs one CTA per SM, which makes this shape slower
+// than the CUDA-core ones, so it is used only on request). When the working matrix fits in shared
 // memory: 3, 4, 5, 6 = 64, 128, 256, 512 threads per CTA (smaller CTAs at small
 // bond dimensions run several samples per SM). 0 (or a variant that does not
 // apply) = the rule above.
@@ -322,21 +323,21 @@ inline cudaError_t choose_launch_shape(int n, int L, int n_clocks, int cap, int 
     ls.x_in_smem = 1;
     ls.x_elems = 4 * cap * cap;
     ls.smem = fixed + xbytes;
-    e = occ(ls.block, ls.smem, &per_sm);
-  } else if (csize == 8 && 2 * cap <= 256 && (variant == 0 || variant == 7) &&
+    e = occ(ls.block, ls.smem, ls.use_tc, &per_sm);
+  } else if (csize == 8 && 2 * cap <= 256 && variant == 7 &&
              fixed + align_up(TcJac::BYTES, 8) <= (size_t)optin) {
     ls.block = TcJac::THREADS;
     ls.x_in_smem = 0;
     ls.x_elems = (int)(align_up(TcJac::BYTES, 8) / 8);
     ls.smem = fixed + (size_t)ls.x_elems * 8;
     ls.use_tc = 1;
-    e = occ(ls.block, ls.smem, &per_sm);
+    e = occ(ls.block, ls.smem, ls.use_tc, &per_sm);
   } else {
     ls.block = 256;
     ls.x_in_smem = 0;
     ls.x_elems = 2 * cap * 32 + 512;
     ls.smem = fixed + (size_t)ls.x_elems * csize;
-    e = ls.smem <= (size_t)optin ? occ(ls.block, ls.smem, &per_sm) : cudaSuccess;
+    e = ls.smem <= (size_t)optin ? occ(ls.block, ls.smem, ls.use_tc, &per_sm) : cudaSuccess;
     if (e != cudaSuccess) return e;
     if (ls.smem > (size_t)optin || (per_sm < 2 && variant != 1) || variant == 2) {
       int bw = 1;
@@ -345,7 +346,7 @@ inline cudaError_t choose_launch_shape(int n, int L, int n_clocks, int cap, int 
       ls.x_elems = 2 * bw * 2 * cap;
       ls.smem = fixed + (size_t)ls.x_elems * csize;
       per_sm = 1;
-      e = occ(ls.block, ls.smem, &per_sm);
+      e = occ(ls.block, ls.smem, ls.use_tc, &per_sm);
     }
   }
   ls.per_sm = per_sm < 1 ? 1 : per_sm;

@@ -110,8 +110,8 @@ __device__ __forceinline__ void stage_update_a(float* hi, float* lo, const float
 // 32 < nc <= 256, m <= 256) through the tensor cores, by a CTA of exactly 8
 // warps (TcJac::THREADS); tol and thr as in Engine::jacobi. Returns the number of sweeps; sets
 // ibuf[1] = 1 on convergence.
-template <typename R>
-__device__ __noinline__ int Engine<R>::jacobi_tc(C* X, int m, int nc, R tol, R thr) {
+template <typename R, bool TC>
+__device__ __noinline__ int Engine<R, TC>::jacobi_tc(C* X, int m, int nc, R tol, R thr) {
   float2* Xf = reinterpret_cast<float2*>(X);
   unsigned char* xs = reinterpret_cast<unsigned char*>(sm.x);
   float2* G = reinterpret_cast<float2*>(xs + TcJac::G_OFF);

@@ -48,8 +48,8 @@ __device__ __forceinline__ void householder_reflector(const cplx<R>* y, int j, i
 // or when tau = 1/(|x|(|x|+|x_0|)) does not fit R: an evolved state carries
 // amplitudes like sin(Delta/2)^k far below 1e-19, and the scale would
 // overflow FP32 (householder_reflector takes the norms themselves in FP64).
-template <typename R>
-__device__ __noinline__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, double tiny2) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::householder(C* Y, int m, int nq, C* Q, double tiny2) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int r = min(m, nq);
   C* vhead = reinterpret_cast<C*>(sm.hh);
@@ -118,8 +118,8 @@ __device__ __noinline__ void Engine<R>::householder(C* Y, int m, int nq, C* Q, d
 }
 
 // Centre c -> c+1: A_c (2 d_c x d_{c+1}) = Q R; A_c <- Q, A_{c+1} <- R A_{c+1}.
-template <typename R>
-__device__ __noinline__ void Engine<R>::qr_right() {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::qr_right() {
   PhaseTimer pt(st, PH_QR);
   const int c = centre;
   if (c < 0 || c > a.n - 2) { fail(ST_BAD_DIM, 3000 + c); return; }
@@ -175,8 +175,8 @@ __device__ __noinline__ void Engine<R>::qr_right() {
 
 // Centre c -> c-1: A_c (d_c x 2 d_{c+1}) = L Q via A_c^H = Q' R;
 // A_c <- Q'^H (right-orthonormal rows), A_{c-1} <- A_{c-1} R^H.
-template <typename R>
-__device__ __noinline__ void Engine<R>::qr_left() {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::qr_left() {
   PhaseTimer pt(st, PH_QR);
   const int c = centre;
   if (c < 1 || c > a.n - 1) { fail(ST_BAD_DIM, 5000 + c); return; }
@@ -231,8 +231,8 @@ __device__ __noinline__ void Engine<R>::qr_left() {
   __syncthreads();
 }
 
-template <typename R>
-__device__ void Engine<R>::move_centre(int target) {
+template <typename R, bool TC>
+__device__ void Engine<R, TC>::move_centre(int target) {
   while (centre < target && !failed()) qr_right();
   while (centre > target && !failed()) qr_left();
 }
@@ -244,8 +244,8 @@ namespace tepai {
 // Compact WY factor of the panel (Schreiber & Van Loan, SIAM J. Sci. Stat.
 // Comput. 10, 1989): H_{j0} ... H_{j0+bp-1} = I - V T V^H with T upper
 // triangular, T_kk = tau_k, T_{0:k,k} = -tau_k T_{0:k,0:k} (V_{:,0:k}^H v_k).
-template <typename R>
-__device__ __noinline__ void Engine<R>::panel_t(const C* V, int m, int j0, int bp, C* T) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::panel_t(const C* V, int m, int j0, int bp, C* T) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const C* tau = reinterpret_cast<const C*>(sm.hh) + 2 * cap;
   // z_{k,jj} = V_{:,k}^H v_jj for k < jj, stored in T[k][jj] (T row-major 16 x 16)
@@ -397,8 +397,8 @@ __device__ __noinline__ void apply_chunk_f32(const float2* V, int m, int bp, con
 // (V[k*m + row], zero above its diagonal, vhead on it). Chunks move by bulk
 // copies; with a second chunk buffer CH1 the load of chunk i+1 overlaps the
 // update of chunk i. Starts and ends with every earlier bulk store drained.
-template <typename R>
-__device__ void Engine<R>::apply_block_reflector(const C* V, int m, int j0, int bp, const C* T, bool herm,
+template <typename R, bool TC>
+__device__ void Engine<R, TC>::apply_block_reflector(const C* V, int m, int j0, int bp, const C* T, bool herm,
                                                  C* G, int c0, int c1, C* CH, C* CH1, C* Wm) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int nch = (c1 - c0 + 15) / 16;
@@ -505,8 +505,8 @@ __device__ __forceinline__ void densify_panel(cplx<R>* P, const cplx<R>* vhead, 
 // Blocked Householder QR of Y (m x nq, column-major, global memory): 16-column
 // panels are factored in shared memory, then the trailing columns are updated
 // with the panel's block reflector. Same output convention as householder().
-template <typename R>
-__device__ __noinline__ void Engine<R>::householder_blocked(C* Y, int m, int nq, C* Q, double tiny2) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::householder_blocked(C* Y, int m, int nq, C* Q, double tiny2) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int r = min(m, nq);
   C* vhead = reinterpret_cast<C*>(sm.hh);

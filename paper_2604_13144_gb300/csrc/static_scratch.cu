@@ -13,8 +13,8 @@
 namespace tepai {
 cudaError_t launch_ensemble_f32(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_ensemble_f64(const KArgs& a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t occupancy_ensemble_f32(int block, size_t smem, int* ctas_per_sm);
-cudaError_t occupancy_ensemble_f64(int block, size_t smem, int* ctas_per_sm);
+cudaError_t occupancy_ensemble_f32(int block, size_t smem, int use_tc, int* ctas_per_sm);
+cudaError_t occupancy_ensemble_f64(int block, size_t smem, int use_tc, int* ctas_per_sm);
 }  // namespace tepai
 
 using namespace tepai;
@@ -92,9 +92,9 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return TEPAI_ERR_CUDA;
-  auto occ = [&](int blk, size_t sm_bytes, int* per) {
-    return Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(blk, sm_bytes, per)
-                                      : occupancy_ensemble_f32(blk, sm_bytes, per);
+  auto occ = [&](int blk, size_t sm_bytes, int use_tc, int* per) {
+    return Q->precision == TEPAI_FP64 ? occupancy_ensemble_f64(blk, sm_bytes, use_tc, per)
+                                      : occupancy_ensemble_f32(blk, sm_bytes, use_tc, per);
   };
   LaunchShape ls{};
   if (choose_launch_shape(hp.n, hp.L, Q->variant == TEPAI_CONTINUOUS ? hp.L : 0, cap, csize, optin, occ, ls, Q->launch_variant) != cudaSuccess)

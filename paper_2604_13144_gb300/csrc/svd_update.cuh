@@ -12,8 +12,8 @@ namespace tepai {
 // when the centre ends on the right site, Z = theta'^T when it ends on the
 // left. With zh set, X receives Z^H instead (the input of the preconditioning
 // QR): theta'^H (ld 2dr) or conj(theta') (ld 2dl).
-template <typename R>
-__device__ __noinline__ void Engine<R>::form_theta(int i, const C g[16], bool end_left, bool zh, C* X) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::form_theta(int i, const C g[16], bool end_left, bool zh, C* X) {
   const int dl = sm.dims[i], dc = sm.dims[i + 1], dr = sm.dims[i + 2];
   const C* A = S(i);
   const C* B = S(i + 1);
@@ -28,8 +28,11 @@ __device__ __noinline__ void Engine<R>::form_theta(int i, const C g[16], bool en
     auto fa = [=](int ii, int kk) { return A[(size_t)ii * dc + kk]; };
     auto fb = [=](int kk, int jj) { return B[(size_t)kk * ncol + jj]; };
     auto fo = [=](int ii, int jj, C v) { thp[(size_t)ii * ncol + jj] = v; };
-    if (tc_worth(m, ncol, dc)) tc_cgemm(m, ncol, dc, fa, fb, fo);
-    else block_gemm<R>(m, ncol, dc, reinterpret_cast<C*>(sm.x), fa, fb, fo);
+    bool done = false;
+    if constexpr (kTC) {
+      if (tc_worth(m, ncol, dc)) { tc_cgemm(m, ncol, dc, fa, fb, fo); done = true; }
+    }
+    if (!done) block_gemm<R>(m, ncol, dc, reinterpret_cast<C*>(sm.x), fa, fb, fo);
     __syncthreads();
   }
   for (int e = tid(); e < dl * dr; e += nt()) {
@@ -286,8 +289,8 @@ __device__ __noinline__ void rr_pass_f32(float2* X, int m, int nc, float tol, fl
 // drift apart and overlap their latency-bound phases, while every pair sees
 // exactly the column values of the barrier-separated schedule. Rotations are
 // counted in ibuf[0].
-template <typename R>
-__device__ __noinline__ void Engine<R>::rr_pass(C* X, int m, int nc, R tol, R thr) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::rr_pass(C* X, int m, int nc, R tol, R thr) {
   if constexpr (sizeof(R) == 4) if (m <= 256 && nc + (nc & 1) <= 2 * cap) {
     float2* xf = reinterpret_cast<float2*>(X);
     if (m <= 64) { if (m == 64) rr_pass_f32<2, true>(xf, m, nc, tol, thr, sm.perm, sm.ibuf);
@@ -327,8 +330,8 @@ __device__ __noinline__ void Engine<R>::rr_pass(C* X, int m, int nc, R tol, R th
 }
 
 // All pairs (p in block A, q in block B): round r pairs p with (p + r) mod nmax.
-template <typename R>
-__device__ __noinline__ void Engine<R>::cross_pass(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::cross_pass(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int nmax = max(na, nb);
   for (int r = 0; r < nmax; ++r) {
@@ -484,9 +487,9 @@ __device__ __noinline__ void cross_pass_f32(float2* XA, int na, float2* XB, int 
 // As in rr_pass, rounds are ordered per column instead of by CTA barriers: B
 // column q is touched by one slot per round, and the slot waits until q has
 // finished the previous round (ver[q], in sm.perm).
-template <typename R>
+template <typename R, bool TC>
 template <int RPL>
-__device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
+__device__ __noinline__ void Engine<R, TC>::cross_pass_regs(C* XA, int na, C* XB, int nb, int m, R tol, R thr) {
   // the column counters live in sm.perm (2 cap entries)
   if constexpr (sizeof(R) == 4) if (max(nb, (int)(nt() >> 5)) <= 2 * cap) {
     float2* xa = reinterpret_cast<float2*>(XA);
@@ -593,8 +596,8 @@ __device__ __noinline__ void Engine<R>::cross_pass_regs(C* XA, int na, C* XB, in
 // the cross pairs and written back, and finally I is written back. Every pair
 // is visited once per sweep. Sweeps stop when one rotates nothing; ibuf[1] = 1
 // then, 0 if the sweep cap was hit.
-template <typename R>
-__device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_smem) {
+template <typename R, bool TC>
+__device__ __noinline__ int Engine<R, TC>::jacobi(C* X, int m, int nc, bool x_in_smem) {
   // rotate a pair when |x_p^H x_q| > tol |x_p||x_q|, tol = a.tol * sqrt(m): the
   // rounding noise of a length-m dot product grows like sqrt(m) eps, so a fixed
   // tolerance would leave the last sweeps rotating pairs on noise alone
@@ -656,7 +659,7 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
   nc = n_act;
   int sweep = 0;
   if (nc < 2) { __syncthreads(); if (tid() == 0) sm.ibuf[1] = 1; __syncthreads(); return 0; }
-  if constexpr (sizeof(R) == 4) {
+  if constexpr (kTC) {
     // single precision, staged in global memory, up to 256 rows and more than
     // one 32-column block: Gram matrices and block updates on the tensor cores
     if (tc_ok && nt() == TcJac::THREADS && !x_in_smem && m <= 256 && nc > 32) {
@@ -764,8 +767,8 @@ __device__ __noinline__ int Engine<R>::jacobi(C* X, int m, int nc, bool x_in_sme
 // rotated when its cosine exceeds 2^-24, the orthogonality FP32 columns can
 // hold, and both columns lie at or above thr. X is in shared memory or, when
 // staged, in global memory with every bulk copy already drained.
-template <typename R>
-__device__ __noinline__ void Engine<R>::reorth_pass_f64(C* X, int m, int nc, bool x_in_smem, double thr) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::reorth_pass_f64(C* X, int m, int nc, bool x_in_smem, double thr) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   const int np = nc + (nc & 1);
   const double tol = 5.9604644775390625e-08;
@@ -811,8 +814,8 @@ __device__ __noinline__ void Engine<R>::reorth_pass_f64(C* X, int m, int nc, boo
 // clear gap (a cut never splits a group of equal singular values), unless no
 // such k' >= 1 exists.
 // The kept values are rescaled to unit norm, so every sample stays normalised.
-template <typename R>
-__device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_left, bool is_swap) {
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::two_site(int i, const C g[16], bool end_left, bool is_swap) {
   if (failed()) return;
   if (i < 0 || i > a.n - 2) { fail(ST_BAD_DIM, i); return; }
   if (centre < i) move_centre(i);
@@ -975,8 +978,11 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
       auto fa = [=](int ii, int kk) { const C u = Ai[(size_t)kk * k + ii]; return C{u.re, -u.im}; };
       auto fb = [=](int kk, int jj) { return thp[(size_t)kk * ncol + jj]; };
       auto fo = [=](int ii, int jj, C v) { Bi[(size_t)ii * ncol + jj] = scale(v, renorm); };
-      if (tc_worth(k, ncol, m)) tc_cgemm(k, ncol, m, fa, fb, fo);
-      else block_gemm<R>(k, ncol, m, reinterpret_cast<C*>(sm.x), fa, fb, fo);
+      bool done = false;
+      if constexpr (kTC) {
+        if (tc_worth(k, ncol, m)) { tc_cgemm(k, ncol, m, fa, fb, fo); done = true; }
+      }
+      if (!done) block_gemm<R>(k, ncol, m, reinterpret_cast<C*>(sm.x), fa, fb, fo);
     } else {
       for (int e = tid(); e < k * ncol; e += nt()) {
         const int mm = e / ncol, col = e - mm * ncol;
@@ -1009,8 +1015,11 @@ __device__ __noinline__ void Engine<R>::two_site(int i, const C g[16], bool end_
       auto fa = [=](int ii, int kk) { return thp[(size_t)ii * ncol + kk]; };
       auto fb = [=](int kk, int jj) { const C u = bip[(size_t)jj * ncol + kk]; return C{u.re, -u.im}; };
       auto fo = [=](int ii, int jj, C v) { Ai[(size_t)ii * k + jj] = scale(v, renorm); };
-      if (tc_worth(rows, k, ncol)) tc_cgemm(rows, k, ncol, fa, fb, fo);
-      else block_gemm<R>(rows, k, ncol, reinterpret_cast<C*>(sm.x), fa, fb, fo);
+      bool done = false;
+      if constexpr (kTC) {
+        if (tc_worth(rows, k, ncol)) { tc_cgemm(rows, k, ncol, fa, fb, fo); done = true; }
+      }
+      if (!done) block_gemm<R>(rows, k, ncol, reinterpret_cast<C*>(sm.x), fa, fb, fo);
     } else {
       for (int e = tid(); e < rows * k; e += nt()) {
         const int row = e / k, mm = e - row * k;

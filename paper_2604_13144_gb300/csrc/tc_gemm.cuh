@@ -50,9 +50,9 @@ __device__ __forceinline__ void tc_stage(float* hi, float* lo, int rows, F f) {
 // chunk c; with one, the other CTA on the SM fills that time. Returns once the
 // accumulator is complete; on a wait that runs out the CTA records
 // ST_MMA_TIMEOUT and failed() is set.
-template <typename R>
+template <typename R, bool TC>
 template <class STAGE>
-__device__ void Engine<R>::tc_pipeline(int N, int nch, bool same, STAGE stage) {
+__device__ void Engine<R, TC>::tc_pipeline(int N, int nch, bool same, STAGE stage) {
   float* base = reinterpret_cast<float*>(sm.x);
   const uint32_t idesc = tc::idesc_tf32(128, N);
   const uint32_t sbo = TcJac::KT * 32;
@@ -91,9 +91,9 @@ __device__ void Engine<R>::tc_pipeline(int N, int nch, bool same, STAGE stage) {
 
 // tc_pipeline with operands given element by element: fa(i, k) and fb(j, k)
 // (callers return 0 outside their extents; k >= K is padded here).
-template <typename R>
+template <typename R, bool TC>
 template <class FA, class FB>
-__device__ void Engine<R>::tc_gemm(int N, int K, bool same, FA fa, FB fb) {
+__device__ void Engine<R, TC>::tc_gemm(int N, int K, bool same, FA fa, FB fb) {
   const int nch = (K + TcJac::KT - 1) / TcJac::KT;
   tc_pipeline(N, nch, same, [&](int c, float* Ahi, float* Alo, float* Bhi, float* Blo) {
     const int k0 = c * TcJac::KT;
@@ -104,8 +104,8 @@ __device__ void Engine<R>::tc_gemm(int N, int K, bool same, FA fa, FB fb) {
 
 // Bounded wait for the latest commit on stage barrier s (idempotent). Returns
 // false after recording ST_MMA_TIMEOUT when the MMAs did not complete.
-template <typename R>
-__device__ bool Engine<R>::tc_wait(int s) {
+template <typename R, bool TC>
+__device__ bool Engine<R, TC>::tc_wait(int s) {
   if (tc_cnt[s] == 0) return true;
   const uint32_t parity = (tc_cnt[s] - 1) & 1u;
   bool ok = false;
@@ -120,9 +120,9 @@ __device__ bool Engine<R>::tc_wait(int s) {
 // one 128-row tile of C and 64 complex columns (128 TMEM columns) at a time.
 // fa(i, k) and fb(k, j) return complex elements (called only inside the
 // extents); fo(i, j, v) stores one. Called by all threads of the CTA.
-template <typename R>
+template <typename R, bool TC>
 template <class FA, class FB, class FO>
-__device__ void Engine<R>::tc_cgemm(int M, int N, int K, FA fa, FB fb, FO fo) {
+__device__ void Engine<R, TC>::tc_cgemm(int M, int N, int K, FA fa, FB fb, FO fo) {
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   for (int m0 = 0; m0 < M && !failed(); m0 += 128) {
     for (int n0 = 0; n0 < N && !failed(); n0 += 64) {

@@ -60,7 +60,7 @@ int main() {
             }
             // launch shapes: a simple occupancy model of the SM (shared memory with
             // 1 KB reserved per CTA, 64K registers at 128 per thread, 2048 threads)
-            auto occ = [&](int block, size_t smem, int* per_sm) {
+            auto occ = [&](int block, size_t smem, int /*use_tc*/, int* per_sm) {
               int by_smem = static_cast<int>(kSmPerSm / (smem + 1024));
               int by_regs = 65536 / (block * 128);
               int by_thr = 2048 / block;

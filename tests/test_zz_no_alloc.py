@@ -1,6 +1,8 @@
 """The entry point that allocates no device memory, for callers that cannot
-call cudaMalloc (graph recording, fixed memory pools, plug-ins that only get
-pre-allocated buffers). Its scratch is a fixed static device array. Its results
+call cudaMalloc: a host application that gives each component a fixed device
+budget, a plug-in that only receives buffers its framework allocated, or code
+that must not pay cudaMalloc's implicit device synchronisation. Its scratch is
+a fixed static device array. Its results
 must equal those of the allocating entry point within the parity tolerances:
 1e-10 in FP64 and 1e-4 in mixed precision. Two calls run back to back,
 because every call reuses the same array."""
