@@ -555,6 +555,7 @@ __device__ __noinline__ void Engine<R, TC>::householder_blocked(C* Y, int m, int
     if (j0 + bp < nq) {
       densify_panel(P, vhead, m, j0, bp);
       panel_t(P, m, j0, bp, T);
+      spt.stop();  // the trailing update is counted apart from the panel
       SubTimer sat(st, SP_QR_APPLY);
       apply_block_reflector(P, m, j0, bp, T, true, Y, j0 + bp, nq, CH, CH1, Wm);
     }
