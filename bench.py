@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--tts-ring32", type=int, default=0, metavar="K",
                     help="also time K full ring32_heisenberg_T2 circuits (chi 64, mixed) and report the "
                          "time-to-<Z> of its 10^4 samples, extrapolated from the K timed ones")
+    ap.add_argument("--three-site", action="store_true",
+                    help="bond-2 gates as one three-site update (tepai_params.three_site) instead of "
+                         "swap routing; compare events/s, not updates/s (each split counts as one update)")
     ap.add_argument("--launch-variant", type=int, default=0,
                     help="tepai_params.launch_variant (0 = library default; 2 = CUDA-core Jacobi, "
                          "7 = tensor-core Jacobi), for A/B runs")
@@ -310,6 +313,8 @@ def run_ours(a):
     prob, par, init = W.bench_workload(batch, window_steps=a.window, chi=a.chi, n=a.n)
     if a.launch_variant:
         par = W.Params(**{**par.__dict__, "launch_variant": a.launch_variant})
+    if a.three_site:
+        par = W.Params(**{**par.__dict__, "three_site": 1})
     stream = torch.cuda.current_stream()
     run = T.DeviceRun(prob, par, init, stream=stream)
     base = 1_000_000 * (rank + 1)
@@ -439,7 +444,8 @@ def run_ours(a):
                                      for k, v in subphases.items()},
                   "cta_busy_frac": sum(phases.values()) / max(kms / 1e3 * SM_MAX_MHZ * 1e6 * grid, 1.0),
                   "kernel_ms": kms, "not_converged": nconv, "fp64_reorth_svds": reorth,
-                  "max_chi": maxchi, "grid_ctas": grid, "tensor_core_jacobi": bool(tcf > 0)},
+                  "max_chi": maxchi, "grid_ctas": grid, "tensor_core_jacobi": bool(tcf > 0),
+                  "three_site": bool(a.three_site)},
     }
     if not a.no_tts and world == 1:
         line["tts_ring8"] = tts_ring8(T, W, torch, local)

@@ -120,6 +120,15 @@ typedef struct {
                                       equal to working precision (1e-12 s_0) are tied. A wider band
                                       (e.g. 1e-4) makes the kept state insensitive to rounding at
                                       nearly degenerate cuts, at the price of discarding them. */
+    int three_site;                /* 1 = a two-site gate between chain positions p and p+2 (ring
+                                      bonds in the folded order) is one three-site update: theta3 =
+                                      A_p A_{p+1} A_{p+2} takes the gate on its outer physical
+                                      indices and two truncated SVDs (2 d_p x 4 d_{p+3}, then
+                                      2 k_1 x 2 d_{p+3}) split it back, each with the keep rule and
+                                      renormalisation of a two-site update (Sec. II.A); the centre
+                                      ends on p+2. 0 = swap routing (swap, gate, swap back: three
+                                      truncated two-site updates). Each split counts as a gate update.
+                                      The arena grows by 16 chi_max^2 values per CTA. */
 } tepai_params;
 
 /* Optional initial MPS shared by all samples (a "hybrid" start). Site tensors
@@ -175,6 +184,7 @@ typedef struct {
                                       pass with FP64 inner products and rotations */
     double tc_flops;               /* flops of the tensor-core MMAs issued (2 M N K per tcgen05.mma;
                                       a 3xTF32 product counts three), 0 on the CUDA-core paths */
+    double three_site_updates;     /* bond-2 gates applied as three-site updates (two splits each) */
 } tepai_stats;
 
 /* Circuit event of one sample: Trotter step j (1-based), term k, setting v

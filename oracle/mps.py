@@ -292,6 +292,8 @@ def apply_event(m: MPS, plan, cache: GateCache, k: int, v: int, chi_max: int,
     assert hi - lo == 2
     if three_site:
         apply_three(m, lo, g, chi_max, cutoff, floor_rel, gap_rel=gap_rel)
+        if regauge:
+            move_centre(m, lo)
         return
     # bring the site at hi next to lo, apply the gate, move it back
     apply_two(m, lo + 1, gates.SWAP, chi_max, cutoff, floor_rel, swap=True, gap_rel=gap_rel,

@@ -79,7 +79,7 @@ Layout layout(const HostPlan& hp, const tepai_params* Q, int grid, bool has_init
   L.sign = o; o = al256(o + (size_t)Q->n_samples * hp.M);
   L.cost = o; o = al256(o + sizeof(int) * (size_t)Q->n_samples);
   L.order = o; o = al256(o + sizeof(int) * (size_t)Q->n_samples);
-  L.stride = al256(((size_t)hp.n * 2 * cap * cap + 8 * cap * cap) * nc.csize);
+  L.stride = al256(((size_t)hp.n * 2 * cap * cap + (Q->three_site ? 24 : 8) * cap * cap) * nc.csize);
   L.arena = o; o = al256(o + L.stride * (size_t)grid);
   // one more arena slot for the canonical form of a shared start state
   L.canon = o; o = al256(o + (has_init ? L.stride : 0));
@@ -248,6 +248,7 @@ int prepare_impl(const tepai_problem* P, const tepai_params* Q, const tepai_mps*
   }
   a.x_in_smem = ls.x_in_smem; a.smem_x_elems = ls.x_elems; a.use_tc = ls.use_tc;
   a.precondition = jacobi_precondition();
+  a.three_site = Q->three_site ? 1 : 0;
   handoff_knob(a);
   if (init) {
     // bring the shared start state to canonical form once; every sample copies it
@@ -450,6 +451,7 @@ int stats_impl(void* ws, tepai_stats* out, cudaStream_t st) {
   out->mean_nu = pr.n_samples > 0 ? (double)ds.events / (double)pr.n_samples : 0.0;
   out->jacobi_reorth = (double)ds.reorth;
   out->tc_flops = ds.tc_flops;
+  out->three_site_updates = (double)ds.three_site;
   return TEPAI_OK;
 }
 

@@ -85,6 +85,7 @@ struct DevStats {
   unsigned long long sub_cycles[SP_N];
   unsigned long long reorth;               // SVDs finished by the FP64 re-orthogonalisation pass
   double tc_flops;                         // flops of the tcgen05 MMAs issued (2 M N K each)
+  unsigned long long three_site;           // bond-2 gates applied as three-site updates
 };
 
 struct KArgs {
@@ -119,6 +120,7 @@ struct KArgs {
   int use_tc;                // 1 = tensor-core Jacobi where it applies (launch shape with its staging room)
   int wait_limit;            // spin iterations of a Jacobi column handoff wait before it gives up
   int wait_bias;             // added to every handoff target (0; tests set it so that no wait is met)
+  int three_site;            // 1 = bond-2 gates as one three-site update (arena holds W3), 0 = swap routing
 };
 
 // Device status codes. A CTA that detects a broken invariant records the first

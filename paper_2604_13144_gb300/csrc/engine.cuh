@@ -5,6 +5,8 @@
 //   TH     4*cap*cap complex: theta' row-major, also QR panel / environments
 //   XG     4*cap*cap complex: SVD working matrix when it does not fit in shared
 //          memory, also the Q factor and temporaries
+//   W3     16*cap*cap complex, only with three-site updates: theta3' of the
+//          first split and its conjugate transpose
 // State in shared memory: bond dims, step flags, sort keys, reductions, and
 // either the whole SVD working matrix X (when it fits) or two staged column
 // blocks of it.
@@ -115,6 +117,7 @@ struct LocalStats {
   unsigned long long sub_cycles[SP_N] = {};
   unsigned long long reorth = 0;
   double tc_flops = 0.0;
+  unsigned long long three_site = 0;
 };
 
 // Adds the SM cycles of a scope to one phase counter (thread 0 only).
@@ -259,6 +262,9 @@ struct Engine {
   }
 
   __device__ __forceinline__ C* S(int i) const { return site0 + (size_t)i * slot; }
+  // three-site buffers (arenas sized with KArgs::three_site): theta3' and its
+  // conjugate transpose, 8 cap^2 complex values each, after XG
+  __device__ __forceinline__ C* W3() const { return XG + (size_t)4 * cap * cap; }
   // Failure state of this CTA (sm.ibuf[15]); uniform across the CTA after a barrier.
   __device__ __forceinline__ bool failed() const { return sm.ibuf[15] != 0; }
   // Record a broken invariant. Called by every thread with uniform arguments.
@@ -381,8 +387,15 @@ struct Engine {
     else
       householder(Y, m, nq, Q, tiny2);
   }
-  // two-site update on bond (i, i+1) with gate g (basis |s_i s_{i+1}>)
-  __device__ void two_site(int i, const C g[16], bool end_left, bool is_swap);
+  // two-site update on bond (i, i+1) with gate g (basis |s_i s_{i+1}>); with
+  // theta_in_th, theta' is already in TH and g is not read
+  __device__ void two_site(int i, const C g[16], bool end_left, bool is_swap, bool theta_in_th = false);
+  // gate g (basis |s_i s_{i+2}>) on positions i, i+2 as one three-site update
+  __device__ void three_site(int i, const C g[16]);
+  __device__ bool svd_truncate(C* Y, C*& X, int& ncx, bool& x_sh, bool pre, bool x_smem, int m, int nc, bool is_swap,
+                               double flops_theta);
+  __device__ void project_left(const C* Ai, int m, int k, const C* theta, int ncol, R renorm, C* out);
+  __device__ void theta_from_th(int dl, int dr, bool end_left, bool zh, C* X);
   __device__ void form_theta(int i, const C g[16], bool end_left, bool zh, C* X);
   __device__ int jacobi(C* X, int m, int nc, bool x_in_smem);
   __device__ int jacobi_tc(C* X, int m, int nc, R tol, R thr);

@@ -176,6 +176,7 @@ __device__ __noinline__ void Engine<R, TC>::apply_event(int k, int v, int& sign_
   // sites are chain positions with T.a < T.b and the gate in basis |s_a s_b>
   if (T.b == T.a + 1) { two_site(T.a, g, false, false); return; }
   if (T.b != T.a + 2) { fail(ST_BAD_DIM, 10000 + k); return; }
+  if (a.three_site) { three_site(T.a, g); return; }
   // two positions apart: bring the site at a+2 next to a, apply, move it back
   C sw[16];
   for (int q = 0; q < 16; ++q) sw[q] = C{0, 0};
@@ -671,6 +672,7 @@ __global__ void __launch_bounds__(512, 1) ensemble_kernel(const __grid_constant_
     for (int p = 0; p < SP_N; ++p) atomicAdd(&a.stats->sub_cycles[p], st.sub_cycles[p]);
     atomicAdd(&a.stats->reorth, st.reorth);
     atomicAdd(&a.stats->tc_flops, st.tc_flops);
+    atomicAdd(&a.stats->three_site, st.three_site);
   }
   if constexpr (TC && sizeof(R) == 4) {
     if (use_tc) {

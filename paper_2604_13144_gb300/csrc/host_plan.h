@@ -158,6 +158,7 @@ inline int build_plan(const tepai_problem* P, const tepai_params* Q, Plan& hp) {
   if (Q->variant < 0 || Q->variant > 3 || Q->precision < 0 || Q->precision > 1) return TEPAI_ERR_INVALID_ARG;
   if (Q->variant == TEPAI_CONTINUOUS && !(Q->delta < M_PI)) return TEPAI_ERR_INVALID_ARG;
   if (Q->launch_variant < 0 || Q->launch_variant > 7) return TEPAI_ERR_INVALID_ARG;
+  if (Q->three_site != 0 && Q->three_site != 1) return TEPAI_ERR_INVALID_ARG;
   if (Q->n_samples < 0 || Q->sample_offset < 0) return TEPAI_ERR_INVALID_ARG;
   const long long S = Q->run_steps ? Q->run_steps : Q->n_steps;
   if (S < 1 || S > Q->n_steps) return TEPAI_ERR_INVALID_ARG;

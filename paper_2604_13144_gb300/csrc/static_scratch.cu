@@ -84,7 +84,7 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
   const size_t o_counter = o; o = a256(o + sizeof(unsigned long long));
   const size_t o_status = o; o = a256(o + 4 * sizeof(int));
   const size_t o_arena = o;
-  const size_t stride = a256(((size_t)hp.n * 2 * cap * cap + 8 * (size_t)cap * cap) * csize);
+  const size_t stride = a256(((size_t)hp.n * 2 * cap * cap + (Q->three_site ? 24 : 8) * (size_t)cap * cap) * csize);
   if (o_arena + stride > kStaticScratchBytes) return TEPAI_ERR_WORKSPACE_TOO_SMALL;
   // launch shape: the same rule as the allocating entry points
   int dev = 0, sms = 0, optin = 0;
@@ -136,6 +136,7 @@ extern "C" int tepai_sample_values_static(const tepai_problem* P, const tepai_pa
   a.status = reinterpret_cast<int*>(base + o_status);
   a.x_in_smem = x_in_smem; a.smem_x_elems = x_elems; a.use_tc = ls.use_tc;
   a.precondition = jacobi_precondition();
+  a.three_site = Q->three_site ? 1 : 0;
   const cudaError_t le = Q->precision == TEPAI_FP64 ? launch_ensemble_f64(a, (int)grid, block, smem, st)
                                                     : launch_ensemble_f32(a, (int)grid, block, smem, st);
   if (le != cudaSuccess) return TEPAI_ERR_CUDA;

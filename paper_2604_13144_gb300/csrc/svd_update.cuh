@@ -803,84 +803,71 @@ __device__ __noinline__ void Engine<R, TC>::reorth_pass_f64(C* X, int m, int nc,
   }
 }
 
-// Gate on bond (i, i+1). The centre is first moved onto site i or i+1, so that
-// theta holds it and the environments are orthonormal (mixed-canonical form).
-// After the SVD the centre sits on site i (end_left) or i+1.
+// SVD and truncation of one working matrix Z (m x nc; its left singular
+// vectors become the orthonormal site). With pre set, Y holds Z^H (nc x m,
+// column-major, destroyed): Z^H = Q R by Householder (Q not formed), then
+// one-sided Jacobi on the columns of X = R^H (Drmac & Veselic, SIAM J. Matrix
+// Anal. Appl. 29, 2008). Z = R^H Q^H, so the normalised columns of X J are the
+// left singular vectors of Z, after far fewer sweeps than Z itself needs.
+// X = R^H goes to shared memory when x_smem is set, replaces R in place when Y
+// is square and in shared memory, and goes to XG otherwise. Without pre, X
+// already holds Z (column-major) and is rotated as it is.
 // Truncation keeps k = max(1, min(chi_max, k_floor, k_cut, min(m, nc))) sorted
 // singular values (descending, ties by column index):
 //   k_cut   = the smallest k with sum_{j>=k} s_j^2 <= cutoff * sum_j s_j^2,
 //   k_floor = #{j : s_j > floor_rel * s_0};
 // then, if s_{k-1} - s_k <= gap_rel * s_0, k drops to the largest k' < k with a
 // clear gap (a cut never splits a group of equal singular values), unless no
-// such k' >= 1 exists.
-// The kept values are rescaled to unit norm, so every sample stays normalised.
+// such k' >= 1 exists. The kept values are rescaled to unit norm, so every
+// sample stays normalised.
+// On return: the singular vectors scaled by the singular values are the
+// columns of X (ncx columns, in shared memory when x_sh), sm.wn their squared
+// norms, sm.perm their ranking, sm.ibuf[2] = k and sm.dbuf[0] = 1/sqrt(kept
+// weight). flops_theta is added to the algorithmic flop count. Returns false
+// after a recorded failure.
 template <typename R, bool TC>
-__device__ __noinline__ void Engine<R, TC>::two_site(int i, const C g[16], bool end_left, bool is_swap) {
-  if (failed()) return;
-  if (i < 0 || i > a.n - 2) { fail(ST_BAD_DIM, i); return; }
-  if (centre < i) move_centre(i);
-  else if (centre > i + 1) move_centre(i + 1);
-  if (failed()) return;
-  const int dl = sm.dims[i], dc = sm.dims[i + 1], dr = sm.dims[i + 2];
-  if (!dim_ok(dl) || !dim_ok(dc) || !dim_ok(dr)) { fail(ST_BAD_DIM, 1000 + i); return; }
-  const int m = end_left ? 2 * dr : 2 * dl;
-  const int nc = end_left ? 2 * dl : 2 * dr;
-  // Preconditioned Jacobi (Drmac & Veselic, SIAM J. Matrix Anal. Appl. 29,
-  // 2008): Z^H = Q R by Householder (Q not formed), then one-sided Jacobi on the
-  // columns of X = R^H. Z = R^H Q^H, so the normalised columns of X J are the
-  // left singular vectors of Z while needing far fewer sweeps than Z itself.
-  // X = R^H lives in shared memory when it fits, or replaces R in place when
-  // Z is square; other shapes run plain Jacobi on Z.
+__device__ __noinline__ bool Engine<R, TC>::svd_truncate(C* Y, C*& X, int& ncx, bool& x_sh, bool pre, bool x_smem,
+                                                         int m, int nc, bool is_swap, double flops_theta) {
   const int r = min(m, nc);
-  const bool y_smem = (m == nc) && (m * nc <= a.smem_x_elems);
-  const bool x_smem = y_smem || (m * r <= a.smem_x_elems);
-  const bool pre = a.precondition && (x_smem || m == nc);
   C* xs = reinterpret_cast<C*>(sm.x);
-  C* X;
-  int ncx;
   if (pre) {
-    C* Y = y_smem ? xs : XG;
-    { PhaseTimer pt(st, PH_THETA); form_theta(i, g, end_left, true, Y); }
-    {
-      PhaseTimer pt(st, PH_QR);
-      double fro = 0.0;
-      for (int e = tid(); e < m * nc; e += nt()) fro += (double)abs2(Y[e]);
-      fro = block_sum(fro, sm.red);
-      // skip only reflectors whose 1/|x|^2 scale would overflow; smaller
-      // columns are still rotated exactly (dropping them would lose their weight)
-      qr_factor(Y, nc, m, nullptr, (sizeof(R) == 4 ? 1e-30 : 1e-280) * fro);
-      const C* alpha = reinterpret_cast<const C*>(sm.hh) + 4 * cap;
-      X = x_smem ? xs : XG;
-      if (X == Y) {
-        // square: move the upper triangle of R to X = R^H in place
-        for (int e = tid(); e < m * m; e += nt()) {
-          const int ca = e / m, rj = e - ca * m;
-          if (ca > rj) {
-            const C u = y_smem ? Y[(size_t)ca * m + rj] : ldcg_c(Y + (size_t)ca * m + rj);
-            X[(size_t)rj * m + ca] = C{u.re, -u.im};
-            X[(size_t)ca * m + rj] = C{0, 0};
-          } else if (ca == rj) {
-            X[(size_t)rj * m + rj] = C{alpha[rj].re, -alpha[rj].im};
-          }
-        }
-      } else {
-        for (int e = tid(); e < m * r; e += nt()) {
-          const int j = e / m, aa = e - j * m;
-          C v = {0, 0};
-          if (aa > j) { const C u = ldcg_c(Y + (size_t)aa * nc + j); v = C{u.re, -u.im}; }
-          else if (aa == j) v = C{alpha[j].re, -alpha[j].im};
-          X[e] = v;
+    PhaseTimer pt(st, PH_QR);
+    double fro = 0.0;
+    for (int e = tid(); e < m * nc; e += nt()) fro += (double)abs2(Y[e]);
+    fro = block_sum(fro, sm.red);
+    // skip only reflectors whose 1/|x|^2 scale would overflow; smaller
+    // columns are still rotated exactly (dropping them would lose their weight)
+    qr_factor(Y, nc, m, nullptr, (sizeof(R) == 4 ? 1e-30 : 1e-280) * fro);
+    const C* alpha = reinterpret_cast<const C*>(sm.hh) + 4 * cap;
+    X = x_smem ? xs : XG;
+    if (X == Y) {
+      // square: move the upper triangle of R to X = R^H in place
+      const bool y_sm = Y == xs;
+      for (int e = tid(); e < m * m; e += nt()) {
+        const int ca = e / m, rj = e - ca * m;
+        if (ca > rj) {
+          const C u = y_sm ? Y[(size_t)ca * m + rj] : ldcg_c(Y + (size_t)ca * m + rj);
+          X[(size_t)rj * m + ca] = C{u.re, -u.im};
+          X[(size_t)ca * m + rj] = C{0, 0};
+        } else if (ca == rj) {
+          X[(size_t)rj * m + rj] = C{alpha[rj].re, -alpha[rj].im};
         }
       }
-      __syncthreads();
+    } else {
+      for (int e = tid(); e < m * r; e += nt()) {
+        const int j = e / m, aa = e - j * m;
+        C v = {0, 0};
+        if (aa > j) { const C u = ldcg_c(Y + (size_t)aa * nc + j); v = C{u.re, -u.im}; }
+        else if (aa == j) v = C{alpha[j].re, -alpha[j].im};
+        X[e] = v;
+      }
     }
+    __syncthreads();
     ncx = r;
   } else {
-    const bool x_in = m * nc <= a.smem_x_elems;
-    X = x_in ? xs : XG;
-    { PhaseTimer pt(st, PH_THETA); form_theta(i, g, end_left, false, X); }
     ncx = nc;
   }
+  if (failed()) return false;
   int sweeps;
   { PhaseTimer pt(st, PH_JACOBI); sweeps = jacobi(X, m, ncx, X == xs); }
   const int converged = sm.ibuf[1];
@@ -888,7 +875,7 @@ __device__ __noinline__ void Engine<R, TC>::two_site(int i, const C g[16], bool 
   SubTimer srt(st, SP_RANK);
   const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
   // squared column norms (FP64 accumulation)
-  const bool x_sh = X == xs;
+  x_sh = X == xs;
   for (int col = w; col < ncx; col += nw) {
     const C* x = X + (size_t)col * m;
     double s2 = 0.0;
@@ -902,7 +889,7 @@ __device__ __noinline__ void Engine<R, TC>::two_site(int i, const C g[16], bool 
   __syncthreads();
   const int bad_norm = sm.ibuf[14];
   __syncthreads();
-  if (bad_norm) { if (tid() == 0) sm.ibuf[14] = 0; fail(ST_NONFINITE, 2000 + i); return; }
+  if (bad_norm) { if (tid() == 0) sm.ibuf[14] = 0; fail(ST_NONFINITE, 2000 + m); return false; }
   for (int j = tid(); j < ncx; j += nt()) sm.perm[j] = -1;
   __syncthreads();
   for (int j = tid(); j < ncx; j += nt()) {
@@ -918,7 +905,7 @@ __device__ __noinline__ void Engine<R, TC>::two_site(int i, const C g[16], bool 
   // the ranks of finite keys form a permutation; check before indexing with it
   int bad_perm = 0;
   for (int j = tid(); j < ncx; j += nt()) bad_perm |= (sm.perm[j] < 0 || sm.perm[j] >= ncx);
-  if (__syncthreads_or(bad_perm)) { fail(ST_BAD_RANK, 9000 + i); return; }
+  if (__syncthreads_or(bad_perm)) { fail(ST_BAD_RANK, 9000 + m); return false; }
   if (tid() == 0) {
     double tot = 0.0;
     for (int j = ncx - 1; j >= 0; --j) tot += sm.wn[sm.perm[j]];
@@ -951,10 +938,56 @@ __device__ __noinline__ void Engine<R, TC>::two_site(int i, const C g[16], bool 
     if (!converged) st.not_converged++;
     if (is_swap) st.swap_updates++; else st.gate_updates++;
     const double mx = (double)max(m, nc), mn = (double)min(m, nc);
-    st.alg_flops += 32.0 * dl * dc * dr + 4.0 * (14.0 * mx * mn * mn + 8.0 * mn * mn * mn);
+    st.alg_flops += flops_theta + 4.0 * (14.0 * mx * mn * mn + 8.0 * mn * mn * mn);
   }
   __syncthreads();
-  srt.stop();
+  return true;
+}
+
+// Gate on bond (i, i+1). The centre is first moved onto site i or i+1, so that
+// theta holds it and the environments are orthonormal (mixed-canonical form).
+// After the SVD (svd_truncate) the centre sits on site i (end_left) or i+1.
+// With theta_in_th the gate is not applied: theta' (2 d_i x 2 d_{i+2},
+// row-major) is already in TH (the second split of a three-site update) and g
+// is not read.
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::two_site(int i, const C g[16], bool end_left, bool is_swap,
+                                                     bool theta_in_th) {
+  if (failed()) return;
+  if (i < 0 || i > a.n - 2) { fail(ST_BAD_DIM, i); return; }
+  if (centre < i) move_centre(i);
+  else if (centre > i + 1) move_centre(i + 1);
+  if (failed()) return;
+  const int dl = sm.dims[i], dc = sm.dims[i + 1], dr = sm.dims[i + 2];
+  if (!dim_ok(dl) || !dim_ok(dc) || !dim_ok(dr)) { fail(ST_BAD_DIM, 1000 + i); return; }
+  const int m = end_left ? 2 * dr : 2 * dl;
+  const int nc = end_left ? 2 * dl : 2 * dr;
+  // X = R^H lives in shared memory when it fits, or replaces R in place when
+  // Z is square; other shapes run plain Jacobi on Z.
+  const int r = min(m, nc);
+  const bool y_smem = (m == nc) && (m * nc <= a.smem_x_elems);
+  const bool x_smem = y_smem || (m * r <= a.smem_x_elems);
+  const bool pre = a.precondition && (x_smem || m == nc);
+  C* xs = reinterpret_cast<C*>(sm.x);
+  C* X;
+  C* Y = nullptr;
+  if (pre) {
+    Y = y_smem ? xs : XG;
+    PhaseTimer pt(st, PH_THETA);
+    if (theta_in_th) theta_from_th(dl, dr, end_left, true, Y);
+    else form_theta(i, g, end_left, true, Y);
+  } else {
+    const bool x_in = m * nc <= a.smem_x_elems;
+    X = x_in ? xs : XG;
+    PhaseTimer pt(st, PH_THETA);
+    if (theta_in_th) theta_from_th(dl, dr, end_left, false, X);
+    else form_theta(i, g, end_left, false, X);
+  }
+  int ncx = 0;
+  bool x_sh = false;
+  const double flops_theta = theta_in_th ? 0.0 : 32.0 * dl * dc * dr;
+  if (!svd_truncate(Y, X, ncx, x_sh, pre, x_smem, m, nc, is_swap, flops_theta)) return;
+  PhaseTimer pt_proj(st, PH_TRUNC);
   SubTimer sjt(st, SP_PROJ);
   const int k = sm.ibuf[2];
   const R renorm = (R)sm.dbuf[0];
@@ -970,28 +1003,7 @@ __device__ __noinline__ void Engine<R, TC>::two_site(int i, const C g[16], bool 
       Ai[e] = scale(ld_x(X + (size_t)col * m + row, x_sh), inv);
     }
     __syncthreads();
-    C* Bi = S(i + 1);
-    const int ncol = 2 * dr;
-    if (a.smem_x_elems >= gemm_tile_elems(nt())) {
-      // Bi = renorm U^H theta' (the working matrix in shared memory is no longer needed)
-      const C* thp = TH;
-      auto fa = [=](int ii, int kk) { const C u = Ai[(size_t)kk * k + ii]; return C{u.re, -u.im}; };
-      auto fb = [=](int kk, int jj) { return thp[(size_t)kk * ncol + jj]; };
-      auto fo = [=](int ii, int jj, C v) { Bi[(size_t)ii * ncol + jj] = scale(v, renorm); };
-      bool done = false;
-      if constexpr (kTC) {
-        if (tc_worth(k, ncol, m)) { tc_cgemm(k, ncol, m, fa, fb, fo); done = true; }
-      }
-      if (!done) block_gemm<R>(k, ncol, m, reinterpret_cast<C*>(sm.x), fa, fb, fo);
-    } else {
-      for (int e = tid(); e < k * ncol; e += nt()) {
-        const int mm = e / ncol, col = e - mm * ncol;
-        C acc2 = {0, 0};
-        for (int row = 0; row < m; ++row) fma_cc(acc2, Ai[(size_t)row * k + mm], TH[(size_t)row * ncol + col]);
-        Bi[e] = scale(acc2, renorm);
-      }
-    }
-    __syncthreads();
+    project_left(Ai, m, k, TH, 2 * dr, renorm, S(i + 1));
     if (tid() == 0) sm.dims[i + 1] = k;
     centre = i + 1;
   } else {
@@ -1035,6 +1047,166 @@ __device__ __noinline__ void Engine<R, TC>::two_site(int i, const C g[16], bool 
     centre = i;
   }
   __syncthreads();
+}
+
+// out = renorm * U^H theta (k x ncol, row-major), with U = Ai (m x k,
+// row-major) and theta (m x ncol, row-major). out must not alias either.
+template <typename R, bool TC>
+__device__ void Engine<R, TC>::project_left(const C* Ai, int m, int k, const C* theta, int ncol, R renorm, C* out) {
+  if (a.smem_x_elems >= gemm_tile_elems(nt())) {
+    // the working matrix in shared memory is no longer needed: it stages the GEMM
+    auto fa = [=](int ii, int kk) { const C u = Ai[(size_t)kk * k + ii]; return C{u.re, -u.im}; };
+    auto fb = [=](int kk, int jj) { return theta[(size_t)kk * ncol + jj]; };
+    auto fo = [=](int ii, int jj, C v) { out[(size_t)ii * ncol + jj] = scale(v, renorm); };
+    bool done = false;
+    if constexpr (kTC) {
+      if (tc_worth(k, ncol, m)) { tc_cgemm(k, ncol, m, fa, fb, fo); done = true; }
+    }
+    if (!done) block_gemm<R>(k, ncol, m, reinterpret_cast<C*>(sm.x), fa, fb, fo);
+  } else {
+    for (int e = tid(); e < k * ncol; e += nt()) {
+      const int mm = e / ncol, col = e - mm * ncol;
+      C acc2 = {0, 0};
+      for (int row = 0; row < m; ++row) fma_cc(acc2, Ai[(size_t)row * k + mm], theta[(size_t)row * ncol + col]);
+      out[e] = scale(acc2, renorm);
+    }
+  }
+  __syncthreads();
+}
+
+// The working matrix of a two-site SVD from a theta' already in TH
+// (2 dl x 2 dr, row-major): the layouts form_theta writes (Z or Z^H, with
+// Z = theta' or theta'^T).
+template <typename R, bool TC>
+__device__ void Engine<R, TC>::theta_from_th(int dl, int dr, bool end_left, bool zh, C* X) {
+  const int m = 2 * dl, ncol = 2 * dr;
+  for (int e = tid(); e < m * ncol; e += nt()) {
+    const int row = e / ncol, col = e - row * ncol;
+    const C o = TH[e];
+    if (!zh) {
+      if (end_left) X[(size_t)row * ncol + col] = o;
+      else X[(size_t)col * m + row] = o;
+    } else {
+      const C oc = {o.re, -o.im};
+      if (end_left) X[(size_t)col * m + row] = oc;
+      else X[(size_t)row * ncol + col] = oc;
+    }
+  }
+  __syncthreads();
+}
+
+// Gate g (basis |s_i s_{i+2}>) on chain positions i and i+2 as one three-site
+// update (the bond-2 alternative to swap routing): with the centre on i, i+1
+// or i+2,
+//   theta3[a, s, t, u, b] = sum_{c,d} A_i[a,s,c] A_{i+1}[c,t,d] A_{i+2}[d,u,b],
+//   M1[(a,x), (t,y,b)]    = sum_{s,u} g[(x,y),(s,u)] theta3[a,s,t,u,b]
+// (2 d_i x 4 d_{i+3}). The first split is the SVD of M1 with the two-site
+// keep rule: site i <- U1 (2 d_i x k1), and renorm * U1^H M1 (k1 x 4 d_{i+3},
+// row-major) is the theta' of bond (i+1, i+2) read as (2 k1 x 2 d_{i+3}).
+// The second split is the two-site SVD of that theta'. The centre ends on i+2.
+// Arena: M1 in W3 (8 cap^2), Y = M1^H in W3 + 8 cap^2 (8 cap^2).
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::three_site(int i, const C g[16]) {
+  if (failed()) return;
+  if (i < 0 || i > a.n - 3) { fail(ST_BAD_DIM, 11000 + i); return; }
+  if (centre < i) move_centre(i);
+  else if (centre > i + 2) move_centre(i + 2);
+  if (failed()) return;
+  const int dl = sm.dims[i], d1 = sm.dims[i + 1], d2 = sm.dims[i + 2], dr = sm.dims[i + 3];
+  if (!dim_ok(dl) || !dim_ok(d1) || !dim_ok(d2) || !dim_ok(dr)) { fail(ST_BAD_DIM, 12000 + i); return; }
+  const int m = 2 * dl, nc = 4 * dr;
+  C* M1 = W3();
+  C* Y = W3() + (size_t)8 * cap * cap;
+  {
+    PhaseTimer pt(st, PH_THETA);
+    const C* A = S(i);
+    const C* B = S(i + 1);
+    const C* Cs = S(i + 2);
+    // T1[(a,s), (t,d)] = A_i (2dl x d1) A_{i+1} (d1 x 2 d2), row-major in TH
+    // T2[(a,s,t), (u,b)] = T1 (4 dl x d2) A_{i+2} (d2 x 2 dr), row-major in Y
+    C* T1 = TH;
+    const bool gemm = a.smem_x_elems >= gemm_tile_elems(nt());
+    {
+      auto fa = [=](int ii, int kk) { return A[(size_t)ii * d1 + kk]; };
+      auto fb = [=](int kk, int jj) { return B[(size_t)kk * 2 * d2 + jj]; };
+      auto fo = [=](int ii, int jj, C v) { T1[(size_t)ii * 2 * d2 + jj] = v; };
+      if (gemm) block_gemm<R>(2 * dl, 2 * d2, d1, reinterpret_cast<C*>(sm.x), fa, fb, fo);
+      else
+        for (int e = tid(); e < 2 * dl * 2 * d2; e += nt()) {
+          const int ii = e / (2 * d2), jj = e - ii * 2 * d2;
+          C acc = {0, 0};
+          for (int kk = 0; kk < d1; ++kk) fma_c(acc, fa(ii, kk), fb(kk, jj));
+          fo(ii, jj, acc);
+        }
+      __syncthreads();
+    }
+    {
+      auto fa = [=](int ii, int kk) { return T1[(size_t)ii * d2 + kk]; };
+      auto fb = [=](int kk, int jj) { return Cs[(size_t)kk * 2 * dr + jj]; };
+      auto fo = [=](int ii, int jj, C v) { Y[(size_t)ii * 2 * dr + jj] = v; };
+      if (gemm) block_gemm<R>(4 * dl, 2 * dr, d2, reinterpret_cast<C*>(sm.x), fa, fb, fo);
+      else
+        for (int e = tid(); e < 4 * dl * 2 * dr; e += nt()) {
+          const int ii = e / (2 * dr), jj = e - ii * 2 * dr;
+          C acc = {0, 0};
+          for (int kk = 0; kk < d2; ++kk) fma_c(acc, fa(ii, kk), fb(kk, jj));
+          fo(ii, jj, acc);
+        }
+      __syncthreads();
+    }
+    // gate on s and u: M1[(a,x), (t,y,b)] = sum_{s,u} g[(x,y),(s,u)] T2[(a,s,t), (u,b)]
+    for (int e = tid(); e < dl * 2 * dr; e += nt()) {
+      const int aa = e / (2 * dr), tb = e - aa * 2 * dr;
+      const int t = tb / dr, bb = tb - t * dr;
+      C tv[4];
+#pragma unroll
+      for (int su = 0; su < 4; ++su) {
+        const int s_ = su >> 1, u = su & 1;
+        tv[su] = Y[(size_t)((aa * 2 + s_) * 2 + t) * 2 * dr + u * dr + bb];
+      }
+#pragma unroll
+      for (int xy = 0; xy < 4; ++xy) {
+        C o = {0, 0};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fma_c(o, g[xy * 4 + q], tv[q]);
+        const int x = xy >> 1, y = xy & 1;
+        M1[(size_t)(aa * 2 + x) * nc + (t * 2 + y) * dr + bb] = o;
+      }
+    }
+    __syncthreads();
+    // Y = Z^H of Z = M1 (nc x m column-major): the conjugate of M1, element by element
+    for (int e = tid(); e < m * nc; e += nt()) { const C o = M1[e]; Y[e] = C{o.re, -o.im}; }
+    __syncthreads();
+  }
+  const bool x_smem = m * m <= a.smem_x_elems;
+  C* X = nullptr;
+  int ncx = 0;
+  bool x_sh = false;
+  const double flops_theta = 32.0 * dl * d1 * d2 + 64.0 * dl * d2 * dr;
+  if (!svd_truncate(Y, X, ncx, x_sh, true, x_smem, m, nc, false, flops_theta)) return;
+  {
+    PhaseTimer pt_proj(st, PH_TRUNC);
+    SubTimer sjt(st, SP_PROJ);
+    const int k1 = sm.ibuf[2];
+    const R renorm = (R)sm.dbuf[0];
+    if (!dim_ok(k1)) { fail(ST_BAD_RANK, k1); return; }
+    // site i <- U1[:, :k1]; TH <- renorm U1^H M1 (k1 x 4 dr)
+    C* Ai = S(i);
+    for (int e = tid(); e < m * k1; e += nt()) {
+      const int row = e / k1, mm = e - row * k1;
+      const int col = sm.perm[mm];
+      const double wv = sm.wn[col];
+      const R inv = wv > 0.0 ? (R)(1.0 / sqrt(wv)) : R(0);
+      Ai[e] = scale(ld_x(X + (size_t)col * m + row, x_sh), inv);
+    }
+    __syncthreads();
+    project_left(Ai, m, k1, M1, nc, renorm, TH);
+    if (tid() == 0) { sm.dims[i + 1] = k1; st.three_site++; }
+    centre = i + 1;
+    __syncthreads();
+  }
+  // second split: theta' of bond (i+1, i+2) = TH as (2 k1) x (2 dr)
+  two_site(i + 1, g, false, false, true);
 }
 
 }  // namespace tepai

@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("n_snapshots", C.c_int), ("obs_sites", C.POINTER(C.c_int)), ("n_obs", C.c_int),
                 ("seed", C.c_ulonglong), ("variant", C.c_int), ("precision", C.c_int),
                 ("launch_variant", C.c_int), ("obs_strings", C.POINTER(C.c_ubyte)),
-                ("tie_rel", C.c_double)]
+                ("tie_rel", C.c_double), ("three_site", C.c_int)]
 
 
 class Mps(C.Structure):
@@ -64,7 +64,8 @@ class Stats(C.Structure):
                 ("grid_ctas", C.c_int), ("jacobi_pairs", C.c_double),
                 ("jacobi_rotations", C.c_double), ("subphase_cycles", C.c_double * 12),
                 ("sample_order", C.c_int), ("seconds", C.c_double), ("mean_nu", C.c_double),
-                ("jacobi_reorth", C.c_double), ("tc_flops", C.c_double)]
+                ("jacobi_reorth", C.c_double), ("tc_flops", C.c_double),
+                ("three_site_updates", C.c_double)]
 
     PHASES = ("init", "sampler", "single_site", "theta", "jacobi", "truncate", "qr", "measure")
     SUBPHASES = ("qr_panel", "qr_apply", "qr_formq", "qr_rmul", "projection", "bulk_wait",
@@ -156,7 +157,7 @@ class Marshalled:
                           int(par.seed) & (2**64 - 1), int(getattr(par, "variant", 0)),
                           int(getattr(par, "precision", 0)), int(getattr(par, "launch_variant", 0)),
                           self.strings.ctypes.data_as(C.POINTER(C.c_ubyte)) if self.strings is not None
-                          else None, float(getattr(par, "tie_rel", 0.0)))
+                          else None, float(getattr(par, "tie_rel", 0.0)), int(getattr(par, "three_site", 0)))
         self.n_obs = nobs if (obs is not None or self.strings is not None) else int(prob.n)
         self.M = int(par.n_snapshots)
         self.init = None

@@ -70,6 +70,10 @@ def test_invalid_arguments_are_rejected(T):
         with pytest.raises(T.TepaiError) as e:
             T.tepai_gnorm(prob, bad)
         assert e.value.code == 1
+    bad = W.Params(**{**par.__dict__, "three_site": 2})     # a flag: 0 or 1
+    with pytest.raises(T.TepaiError) as e:
+        T.tepai_gnorm(prob, bad)
+    assert e.value.code == 1
     trot = W.Params(**{**par.__dict__, "n_steps": 100, "variant": 2})   # Trotter has no Delta bound
     g, nu = T.tepai_gnorm(prob, trot)
     assert np.all(g == 1.0) and nu == 100 * 32

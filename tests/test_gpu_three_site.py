@@ -1,0 +1,101 @@
+"""Bond-2 gates as one three-site update on the device (tepai_params.three_site),
+against the oracle's three-site update (oracle/mps.py apply_three) and, where
+nothing is truncated, against the exact state vector: 1e-10 in FP64 and 1e-4
+in mixed precision on every <Z_i>.
+
+Cases: the ring-of-8 workload (chi 16, nothing truncated, every ring bond a
+bond-2 gate in the folded order); a truncated ring of 10 at chi 6; and random
+MPS at the cap chi = 128 on a ring of 16, where the first split's matrix is
+256 x 512 (its preconditioning QR factors 512 rows) and the second split runs
+the staged two-site path."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle_rule import oracle_rule
+from oracle import run as oracle_run
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOLMIX = 1e-10, 1e-4
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2604_13144_gb300 import build
+    build.build()
+    from paper_2604_13144_gb300 import tepai
+    return tepai
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    c = T.tepai_create(0)
+    yield c
+    T.tepai_destroy(c)
+
+
+def _three(par):
+    return W.Params(**{**par.__dict__, "three_site": 1})
+
+
+def _check_stats(st):
+    assert st["device_status"][0] == 0, st["device_status"]
+    assert st["three_site_updates"] > 0
+    assert st["swap_updates"] == 0
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMIX)])
+def test_ring8_three_site_matches_statevector_and_oracle(T, ctx, precision, tol):
+    prob, par, _ = W.workload(W.RING8)
+    par = _three(W.Params(**{**par.__dict__, "n_samples": 4, "obs_sites": None, "precision": precision}))
+    got = T.tepai_sample_values(ctx, prob, par)
+    _check_stats(got["stats"])
+    sv = oracle_run.run(prob, par, use_statevector=True, **oracle_rule(par))
+    ref = oracle_run.run(prob, par, three_site=True, **oracle_rule(par))
+    assert np.array_equal(got["sign"], sv["sign"])
+    assert np.max(np.abs(got["v"] - sv["v"])) <= tol
+    assert np.max(np.abs(got["v"] - ref["v"])) <= tol
+    # each bond-2 event is two splits instead of three updates
+    st = got["stats"]
+    assert st["gate_updates"] >= 2 * st["three_site_updates"]
+
+
+def test_truncated_ring10_three_site_fp64(T, ctx):
+    """chi 6 on a ring of 10: both splits truncate. Values that the oracle
+    fixes (its run in another exact gauge agrees to 1e-11) are held to 1e-10,
+    the others to 4 times the oracle's own spread."""
+    prob = W.spin_ring(10, 1.0, seed=4)
+    par = _three(W.Params(T=0.5, n_steps=200, delta=math.pi / 64, n_samples=6, chi_max=6, cutoff=1e-12,
+                          n_snapshots=4, seed=5, precision=0))
+    got = T.tepai_sample_values(ctx, prob, par)
+    _check_stats(got["stats"])
+    ref = oracle_run.run(prob, par, three_site=True, **oracle_rule(par))
+    alt = oracle_run.run(prob, par, three_site=True, regauge=True, **oracle_rule(par))
+    assert np.array_equal(got["sign"], ref["sign"])
+    assert max(s["max_discarded"] for s in ref["stats"]) > 0.0
+    err = np.max(np.abs(got["v"] - ref["v"]), axis=2)
+    d = np.max(np.abs(alt["v"] - ref["v"]), axis=2)
+    fixed = d <= TOL64 / 10
+    print("fixed", int(fixed.sum()), "of", fixed.size, "worst held", float(err[fixed].max(initial=0.0)))
+    assert fixed.sum() >= fixed.size // 2
+    assert np.all(err[fixed] <= TOL64)
+    assert np.all(err[~fixed] <= 4 * d[~fixed])
+
+
+@pytest.mark.parametrize("precision,tol,cutoff", [(1, TOLMIX, 1e-10), (0, TOL64, 0.0)])
+def test_chi128_three_site_staged(T, ctx, precision, tol, cutoff):
+    prob = W.spin_ring(16, 1.0, seed=5, Jz=0.5)
+    tens, dims = W.random_mps_tensors(16, 128, seed=105)
+    par = _three(W.Params(T=3.0, n_steps=18000, delta=math.pi / 1024, n_samples=2, chi_max=128,
+                          cutoff=cutoff, n_snapshots=1, seed=7, precision=precision, run_steps=1))
+    got = T.tepai_sample_values(ctx, prob, par, (tens, dims))
+    _check_stats(got["stats"])
+    ref = oracle_run.run(prob, par, init_tensors=tens, three_site=True, **oracle_rule(par))
+    assert max(s["three_site_updates"] for s in ref["stats"]) > 0
+    assert np.array_equal(got["sign"], ref["sign"])
+    err = np.max(np.abs(got["v"] - ref["v"]))
+    print("chi 128 three-site, precision", precision, "max err", err, "max chi", got["stats"]["max_chi"])
+    assert err <= tol

@@ -54,6 +54,7 @@ class Params:
                                            # replaces obs_sites when given
     tie_rel: float = 0.0      # tie band at truncation cuts (0 = only equal values are tied)
     launch_variant: int = 0   # launch shape of the CUDA path (0 = its default rule)
+    three_site: int = 0       # 1 = bond-2 gates as one three-site update (0 = swap routing)
 
     def steps_run(self) -> int:
         return self.n_steps if self.run_steps == 0 else self.run_steps
