@@ -372,6 +372,7 @@ struct Engine {
   __device__ void qr_right();
   __device__ void qr_left();
   __device__ void householder(C* Y, int m, int nq, C* Q, double tiny2);
+  __device__ void ts_combine(C* Tm, C* Bm, int ld, int n, double tiny2);
   __device__ void householder_blocked(C* Y, int m, int nq, C* Q, double tiny2);
   __device__ void panel_t(const C* V, int m, int j0, int bp, C* T);
   __device__ void apply_block_reflector(const C* V, int m, int j0, int bp, const C* T, bool herm,
@@ -393,7 +394,7 @@ struct Engine {
   // gate g (basis |s_i s_{i+2}>) on positions i, i+2 as one three-site update
   __device__ void three_site(int i, const C g[16]);
   __device__ bool svd_truncate(C* Y, C*& X, int& ncx, bool& x_sh, bool pre, bool x_smem, int m, int nc, bool is_swap,
-                               double flops_theta);
+                               double flops_theta, bool factored = false, int y_ld = 0);
   __device__ void project_left(const C* Ai, int m, int k, const C* theta, int ncol, R renorm, C* out);
   __device__ void theta_from_th(int dl, int dr, bool end_left, bool zh, C* X);
   __device__ void form_theta(int i, const C g[16], bool end_left, bool zh, C* X);

@@ -5,15 +5,34 @@
 
 namespace tepai {
 
-// Reflector of column y at row j (rows j..m-1, warp-collective; lane 0 writes
-// vhead[j], tau[j] and alpha[j]). Squares, sums, |x_0| and the phase
-// x_0 / |x_0| are taken in FP64 whatever R is: the square of an FP32 entry
-// below about 1e-19 falls into the subnormal range and keeps only a few
-// significant bits, and a norm or phase taken from it would make
-// I - tau v v^H non-unitary (tau |v|^2 != 2), so that a Q formed from it is no
-// longer an isometry. In FP64 the squares of FP32 values are always exact
-// enough. The reflector is skipped (tau = 0, H = I) when the column's |x|^2 is
-// at most tiny2 or tau does not fit R.
+// Reflector of a column x with |x|^2 = nr2 and leading entry x_0: vhead,
+// tau and alpha of H = I - tau v v^H, H x = alpha e_0. Squares, sums, |x_0|
+// and the phase x_0 / |x_0| are taken in FP64 whatever R is: the square of an
+// FP32 entry below about 1e-19 falls into the subnormal range and keeps only a
+// few significant bits, and a norm or phase taken from it would make H
+// non-unitary (tau |v|^2 != 2), so that a Q formed from it is no longer an
+// isometry. In FP64 the squares of FP32 values are always exact enough. The
+// reflector is skipped (tau = 0, H = I) when |x|^2 is at most tiny2 or tau
+// does not fit R.
+template <typename R>
+__device__ __forceinline__ void reflector_params(double nr2, cplx<R> x0, double tiny2, cplx<R>& vhead,
+                                                 cplx<R>& tau, cplx<R>& alpha) {
+  const double xr = (double)x0.re, xi = (double)x0.im;
+  const double ax0 = sqrt(fma(xr, xr, xi * xi));
+  const double nrm = sqrt(nr2);
+  const double tj = 1.0 / (nrm * (nrm + ax0));
+  if (!(nr2 > tiny2) || !(nrm > 0.0) || !isfinite((R)tj)) {
+    vhead = cplx<R>{1, 0}; tau = cplx<R>{0, 0}; alpha = x0;
+    return;
+  }
+  const double pr = ax0 > 0.0 ? xr / ax0 : 1.0, pi = ax0 > 0.0 ? xi / ax0 : 0.0;
+  alpha = cplx<R>{(R)(-pr * nrm), (R)(-pi * nrm)};
+  vhead = cplx<R>{(R)(pr * (ax0 + nrm)), (R)(pi * (ax0 + nrm))};
+  tau = cplx<R>{(R)tj, 0};
+}
+
+// Reflector of column y at row j (rows j..m-1, warp-collective, norms in
+// FP64; lane 0 writes vhead[j], tau[j] and alpha[j]).
 template <typename R>
 __device__ __forceinline__ void householder_reflector(const cplx<R>* y, int j, int m, int lane, double tiny2,
                                                       cplx<R>* vhead, cplx<R>* tau, cplx<R>* alpha) {
@@ -23,20 +42,7 @@ __device__ __forceinline__ void householder_reflector(const cplx<R>* y, int j, i
     nr2 = fma(re, re, fma(im, im, nr2));
   }
   nr2 = warp_sum(nr2);
-  if (lane != 0) return;
-  const cplx<R> x0 = y[j];
-  const double xr = (double)x0.re, xi = (double)x0.im;
-  const double ax0 = sqrt(fma(xr, xr, xi * xi));
-  const double nrm = sqrt(nr2);
-  const double tj = 1.0 / (nrm * (nrm + ax0));
-  if (!(nr2 > tiny2) || !(nrm > 0.0) || !isfinite((R)tj)) {
-    vhead[j] = cplx<R>{1, 0}; tau[j] = cplx<R>{0, 0}; alpha[j] = x0;
-    return;
-  }
-  const double pr = ax0 > 0.0 ? xr / ax0 : 1.0, pi = ax0 > 0.0 ? xi / ax0 : 0.0;
-  alpha[j] = cplx<R>{(R)(-pr * nrm), (R)(-pi * nrm)};
-  vhead[j] = cplx<R>{(R)(pr * (ax0 + nrm)), (R)(pi * (ax0 + nrm))};
-  tau[j] = cplx<R>{(R)tj, 0};
+  if (lane == 0) reflector_params<R>(nr2, y[j], tiny2, vhead[j], tau[j], alpha[j]);
 }
 
 // Householder QR of Y (m x nq, column-major, ld m): Y = Q R with r = min(m, nq).
@@ -577,6 +583,62 @@ __device__ __noinline__ void Engine<R, TC>::householder_blocked(C* Y, int m, int
     apply_block_reflector(P, m, j0, bp, T, false, Q, j0, r, CH, CH1, Wm);
   }
   (void)alpha;
+}
+
+// The triangle-on-triangle step of a two-level QR: the R factor of
+// S = [T; B], where T and B are n x n upper-triangular (column-major, leading
+// dimension ld, diagonal included in the arrays; entries below the diagonal
+// are ignored). Column j's reflector (householder_reflector's convention)
+// maps (T[j][j], B[0..j][j]) onto alpha_j e_j: every other entry of that
+// column of S is zero, so step j costs O(j (n - j)) instead of O((2n - j)(n - j)).
+// On return the strict upper triangle of R is in T and its diagonal in the
+// alpha array (sm.hh + 4 cap), as householder() leaves them.
+template <typename R, bool TC>
+__device__ __noinline__ void Engine<R, TC>::ts_combine(C* Tm, C* Bm, int ld, int n, double tiny2) {
+  SubTimer spt(st, SP_QR_PANEL);
+  const int lane = tid() & 31, w = tid() >> 5, nw = nt() >> 5;
+  C* vhead = reinterpret_cast<C*>(sm.hh);
+  C* tau = vhead + 2 * cap;
+  C* alpha = tau + 2 * cap;
+  for (int j = 0; j < n; ++j) {
+    const C* bj = Bm + (size_t)j * ld;
+    if (w == 0) {
+      double nr2 = 0.0;
+      for (int b = lane; b <= j; b += 32) {
+        const double re = (double)bj[b].re, im = (double)bj[b].im;
+        nr2 = fma(re, re, fma(im, im, nr2));
+      }
+      const C x0 = Tm[(size_t)j * ld + j];
+      if (lane == 0) nr2 += fma((double)x0.re, (double)x0.re, (double)x0.im * (double)x0.im);
+      nr2 = warp_sum(nr2);
+      if (lane == 0) reflector_params<R>(nr2, x0, tiny2, vhead[j], tau[j], alpha[j]);
+    }
+    __syncthreads();
+    const C vh = vhead[j];
+    const R tj = tau[j].re;
+    if (tj != R(0)) {
+      for (int c = j + 1 + w; c < n; c += nw) {
+        C* tcol = Tm + (size_t)c * ld;
+        C* bc = Bm + (size_t)c * ld;
+        R sr = 0, si = 0;
+        if (lane == 0) {
+          const C yy = tcol[j];
+          sr = vh.re * yy.re + vh.im * yy.im;
+          si = vh.re * yy.im - vh.im * yy.re;
+        }
+        for (int b = lane; b <= j; b += 32) {
+          const C vv = bj[b], yy = bc[b];
+          sr = fma(vv.re, yy.re, fma(vv.im, yy.im, sr));
+          si = fma(vv.re, yy.im, fma(-vv.im, yy.re, si));
+        }
+        sr = warp_sum(sr) * tj; si = warp_sum(si) * tj;
+        const C sc = {sr, si};
+        if (lane == 0) tcol[j] = sub(tcol[j], mul(vh, sc));
+        for (int b = lane; b <= j; b += 32) bc[b] = sub(bc[b], mul(bj[b], sc));
+      }
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace tepai

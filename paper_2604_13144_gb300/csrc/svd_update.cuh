@@ -823,21 +823,27 @@ __device__ __noinline__ void Engine<R, TC>::reorth_pass_f64(C* X, int m, int nc,
 // On return: the singular vectors scaled by the singular values are the
 // columns of X (ncx columns, in shared memory when x_sh), sm.wn their squared
 // norms, sm.perm their ranking, sm.ibuf[2] = k and sm.dbuf[0] = 1/sqrt(kept
-// weight). flops_theta is added to the algorithmic flop count. Returns false
+// weight). flops_theta is added to the algorithmic flop count. With factored
+// set, Y already holds R (strict upper triangle, leading dimension y_ld;
+// diagonal in the alpha array), and the QR is not run again. Returns false
 // after a recorded failure.
 template <typename R, bool TC>
 __device__ __noinline__ bool Engine<R, TC>::svd_truncate(C* Y, C*& X, int& ncx, bool& x_sh, bool pre, bool x_smem,
-                                                         int m, int nc, bool is_swap, double flops_theta) {
+                                                         int m, int nc, bool is_swap, double flops_theta,
+                                                         bool factored, int y_ld) {
   const int r = min(m, nc);
   C* xs = reinterpret_cast<C*>(sm.x);
   if (pre) {
     PhaseTimer pt(st, PH_QR);
-    double fro = 0.0;
-    for (int e = tid(); e < m * nc; e += nt()) fro += (double)abs2(Y[e]);
-    fro = block_sum(fro, sm.red);
-    // skip only reflectors whose 1/|x|^2 scale would overflow; smaller
-    // columns are still rotated exactly (dropping them would lose their weight)
-    qr_factor(Y, nc, m, nullptr, (sizeof(R) == 4 ? 1e-30 : 1e-280) * fro);
+    if (!factored) {
+      double fro = 0.0;
+      for (int e = tid(); e < m * nc; e += nt()) fro += (double)abs2(Y[e]);
+      fro = block_sum(fro, sm.red);
+      // skip only reflectors whose 1/|x|^2 scale would overflow; smaller
+      // columns are still rotated exactly (dropping them would lose their weight)
+      qr_factor(Y, nc, m, nullptr, (sizeof(R) == 4 ? 1e-30 : 1e-280) * fro);
+    }
+    const int ld = y_ld > 0 ? y_ld : nc;
     const C* alpha = reinterpret_cast<const C*>(sm.hh) + 4 * cap;
     X = x_smem ? xs : XG;
     if (X == Y) {
@@ -857,7 +863,7 @@ __device__ __noinline__ bool Engine<R, TC>::svd_truncate(C* Y, C*& X, int& ncx, 
       for (int e = tid(); e < m * r; e += nt()) {
         const int j = e / m, aa = e - j * m;
         C v = {0, 0};
-        if (aa > j) { const C u = ldcg_c(Y + (size_t)aa * nc + j); v = C{u.re, -u.im}; }
+        if (aa > j) { const C u = ldcg_c(Y + (size_t)aa * ld + j); v = C{u.re, -u.im}; }
         else if (aa == j) v = C{alpha[j].re, -alpha[j].im};
         X[e] = v;
       }
@@ -1104,7 +1110,8 @@ __device__ void Engine<R, TC>::theta_from_th(int dl, int dr, bool end_left, bool
 // keep rule: site i <- U1 (2 d_i x k1), and renorm * U1^H M1 (k1 x 4 d_{i+3},
 // row-major) is the theta' of bond (i+1, i+2) read as (2 k1 x 2 d_{i+3}).
 // The second split is the two-site SVD of that theta'. The centre ends on i+2.
-// Arena: M1 in W3 (8 cap^2), Y = M1^H in W3 + 8 cap^2 (8 cap^2).
+// Arena: M1 in W3 (8 cap^2), Y = M1^H in W3 + 8 cap^2 (8 cap^2), or its two
+// row halves at W3 + 8 cap^2 and W3 + 12 cap^2 for the two-level QR.
 template <typename R, bool TC>
 __device__ __noinline__ void Engine<R, TC>::three_site(int i, const C g[16]) {
   if (failed()) return;
@@ -1117,6 +1124,10 @@ __device__ __noinline__ void Engine<R, TC>::three_site(int i, const C g[16]) {
   const int m = 2 * dl, nc = 4 * dr;
   C* M1 = W3();
   C* Y = W3() + (size_t)8 * cap * cap;
+  // two-level QR when Z^H's two row halves (2 dr x 2 dl each) are at least square
+  const bool two_level = dr >= dl;
+  C* Yt = Y;
+  C* Yb = Y + (size_t)4 * cap * cap;
   {
     PhaseTimer pt(st, PH_THETA);
     const C* A = S(i);
@@ -1174,16 +1185,51 @@ __device__ __noinline__ void Engine<R, TC>::three_site(int i, const C g[16]) {
       }
     }
     __syncthreads();
-    // Y = Z^H of Z = M1 (nc x m column-major): the conjugate of M1, element by element
-    for (int e = tid(); e < m * nc; e += nt()) { const C o = M1[e]; Y[e] = C{o.re, -o.im}; }
+    // Y = Z^H of Z = M1 (nc x m column-major): the conjugate of M1, element by
+    // element. For the two-level QR its rows are split into two halves of
+    // 2 dr rows, each column-major with leading dimension 2 dr.
+    if (!two_level) {
+      for (int e = tid(); e < m * nc; e += nt()) { const C o = M1[e]; Y[e] = C{o.re, -o.im}; }
+    } else {
+      const int h = 2 * dr;
+      for (int e = tid(); e < m * nc; e += nt()) {
+        const int aa = e / nc, c = e - aa * nc;
+        const C o = M1[e];
+        (c < h ? Yt : Yb)[(size_t)aa * h + (c < h ? c : c - h)] = C{o.re, -o.im};
+      }
+    }
     __syncthreads();
+  }
+  if (two_level) {
+    // Two-level QR of Z^H (4 dr x 2 dl): the R factors of its two row halves
+    // (blocked Householder where the staging room allows), then the R of the
+    // stacked pair (ts_combine). Only R is needed: the Jacobi yields U1.
+    PhaseTimer pt(st, PH_QR);
+    double fro = 0.0;
+    for (int e = tid(); e < m * nc; e += nt()) fro += (double)abs2(M1[e]);
+    fro = block_sum(fro, sm.red);
+    const double tiny2 = (sizeof(R) == 4 ? 1e-30 : 1e-280) * fro;
+    const int h = 2 * dr;
+    C* alpha = reinterpret_cast<C*>(sm.hh) + 4 * cap;
+    for (int half = 0; half < 2 && !failed(); ++half) {
+      C* Yh = half ? Yb : Yt;
+      qr_factor(Yh, h, m, nullptr, tiny2);
+      if (failed()) return;
+      // the diagonal of this half's R into its array (the next QR reuses alpha)
+      for (int j = tid(); j < m; j += nt()) Yh[(size_t)j * h + j] = alpha[j];
+      __syncthreads();
+    }
+    if (failed()) return;
+    ts_combine(Yt, Yb, h, m, tiny2);
   }
   const bool x_smem = m * m <= a.smem_x_elems;
   C* X = nullptr;
   int ncx = 0;
   bool x_sh = false;
   const double flops_theta = 32.0 * dl * d1 * d2 + 64.0 * dl * d2 * dr;
-  if (!svd_truncate(Y, X, ncx, x_sh, true, x_smem, m, nc, false, flops_theta)) return;
+  if (!svd_truncate(two_level ? Yt : Y, X, ncx, x_sh, true, x_smem, m, nc, false, flops_theta, two_level,
+                    two_level ? 2 * dr : 0))
+    return;
   {
     PhaseTimer pt_proj(st, PH_TRUNC);
     SubTimer sjt(st, SP_PROJ);
