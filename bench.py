@@ -31,6 +31,14 @@ sys.path.insert(0, ROOT)
 METRIC = "TE-PAI MPS gate-updates/s at chi=128"
 UNIT = "updates/s"
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) per two-site update of the ensemble kernel on this
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# one pass, -k ensemble_kernel -c 1) of a 304-sample batch of the same ring of
+# 64 at chi = 128: 3.728e11 + 4.921e11 bytes over 15716 updates. The launch
+# runs the same 304 CTAs as the full batch, so the bytes per update carry over;
+# the line's traffic is this times the updates of one launch.
+# (profiles/ensemble_kernel_ring64_chi128_launches.md gives the command.)
+DRAM_BYTES_PER_UPDATE = 5.503e7
 
 
 def parse():
@@ -54,6 +62,9 @@ def parse():
     ap.add_argument("--three-site", action="store_true",
                     help="bond-2 gates as one three-site update (tepai_params.three_site) instead of "
                          "swap routing; compare events/s, not updates/s (each split counts as one update)")
+    ap.add_argument("--three-site-steps", type=int, default=2,
+                    help="also time this many steps of the same circuits with three-site updates "
+                         "(0 = skip); reported as the line's three_site object")
     ap.add_argument("--launch-variant", type=int, default=0,
                     help="tepai_params.launch_variant (0 = library default; 2 = CUDA-core Jacobi, "
                          "7 = tensor-core Jacobi), for A/B runs")
@@ -319,14 +330,15 @@ def run_ours(a):
     run = T.DeviceRun(prob, par, init, stream=stream)
     base = 1_000_000 * (rank + 1)
 
-    def step(i):
-        run.set_sample_offset(base + i * batch)
+    def step(i, r=None):
+        r = r or run
+        r.set_sample_offset(base + i * batch)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        run.execute()
+        r.execute()
         e1.record(stream)
-        st = run.stats()            # synchronises the stream
+        st = r.stats()              # synchronises the stream
         if st["device_status"][0] != 0:
             raise RuntimeError(f"device check failed: {st['device_status']}")
         return e0.elapsed_time(e1), st
@@ -380,6 +392,33 @@ def run_ours(a):
         upd_all = upd
     value = upd_all / elapsed
 
+    # the same circuits (the first timed steps' samples) with bond-2 gates as
+    # three-site updates instead of swap routing: sampled events/s is the rate
+    # to compare, since a three-site update counts two splits per event where
+    # swap routing counts three updates
+    three = None
+    if world == 1 and not a.three_site and a.three_site_steps > 0:
+        run3 = T.DeviceRun(prob, W.Params(**{**par.__dict__, "three_site": 1}), init, stream=stream)
+        step(0, run3)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        ev3, up3, k3 = 0.0, 0.0, 0.0
+        n3 = min(a.three_site_steps, a.steps)
+        for i in range(n3):
+            ms, st = step(a.warmup + i, run3)
+            k3 += ms
+            ev3 += st["events"]
+            up3 += st["gate_updates"] + st["swap_updates"]
+        torch.cuda.synchronize()
+        el3 = time.perf_counter() - t3
+        run3.release()
+        del run3
+        three = {"events_per_s": ev3 / el3, "updates_per_s": up3 / el3, "steps": n3,
+                 "ms_per_step": 1e3 * el3 / n3, "kernel_ms": k3,
+                 "events_per_s_swap_routing": events / elapsed,
+                 "events_speedup": (ev3 / el3) / max(events / elapsed, 1e-30),
+                 "note": "tepai_params.three_site = 1 on the samples of the first timed steps"}
+
     # end-to-end through the C-ABI with host buffers (planning, H2D, kernels, D2H)
     ctx = T.tepai_create(local, stream.cuda_stream)
     e2e_par = W.Params(**{**par.__dict__, "sample_offset": base + 500_000})
@@ -423,7 +462,10 @@ def run_ours(a):
         "gpu_launches": (2 + 2 * order_on) * a.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": DRAM_BYTES_PER_UPDATE * upd / a.steps,
+                     "traffic_note": "DRAM bytes per launch: ncu bytes per update on a 304-sample batch of this "
+                                     "workload x updates per launch; algorithmic site-tensor bytes are 64 chi^2 "
+                                     "= 1.05 MB per update",
                      "peak_note": "FP32 FMA throughput of this GPU, measured (tepai_measure_peaks); "
                                   "achieved = algorithmic flops (736 chi^3 per square update) per second "
                                   "of ensemble-kernel time"},
@@ -447,6 +489,8 @@ def run_ours(a):
                   "max_chi": maxchi, "grid_ctas": grid, "tensor_core_jacobi": bool(tcf > 0),
                   "three_site": bool(a.three_site)},
     }
+    if three is not None:
+        line["three_site"] = three
     if not a.no_tts and world == 1:
         line["tts_ring8"] = tts_ring8(T, W, torch, local)
     if a.tts_ring32 and world == 1:

@@ -18,7 +18,22 @@ template <typename R>
 __device__ __forceinline__ void reflector_params(double nr2, cplx<R> x0, double tiny2, cplx<R>& vhead,
                                                  cplx<R>& tau, cplx<R>& alpha) {
   const double xr = (double)x0.re, xi = (double)x0.im;
-  const double ax0 = sqrt(fma(xr, xr, xi * xi));
+  const double a2 = fma(xr, xr, xi * xi);
+  if constexpr (sizeof(R) == 4) {
+    // FP32 square root and divisions (FP64 ones are long sequences on this
+    // part) wherever |x|^2 and |x_0|^2 (unless x_0 = 0) are normal FP32 numbers
+    // far from both ends of the range: then they hold full relative precision
+    if (nr2 > tiny2 && nr2 >= 1e-30 && nr2 <= 1e30 && (a2 == 0.0 || a2 >= 1e-30)) {
+      const float ax0 = sqrtf((float)a2), nrm = sqrtf((float)nr2);
+      const float tj = 1.0f / (nrm * (nrm + ax0));
+      const float pr = ax0 > 0.f ? x0.re / ax0 : 1.f, pi = ax0 > 0.f ? x0.im / ax0 : 0.f;
+      alpha = cplx<R>{-pr * nrm, -pi * nrm};
+      vhead = cplx<R>{pr * (ax0 + nrm), pi * (ax0 + nrm)};
+      tau = cplx<R>{tj, 0};
+      return;
+    }
+  }
+  const double ax0 = sqrt(a2);
   const double nrm = sqrt(nr2);
   const double tj = 1.0 / (nrm * (nrm + ax0));
   if (!(nr2 > tiny2) || !(nrm > 0.0) || !isfinite((R)tj)) {
@@ -31,17 +46,28 @@ __device__ __forceinline__ void reflector_params(double nr2, cplx<R> x0, double 
   tau = cplx<R>{(R)tj, 0};
 }
 
-// Reflector of column y at row j (rows j..m-1, warp-collective, norms in
-// FP64; lane 0 writes vhead[j], tau[j] and alpha[j]).
+// Reflector of column y at row j (rows j..m-1, warp-collective; lane 0 writes
+// vhead[j], tau[j] and alpha[j]). In single precision |x|^2 is summed in FP32
+// first: when the sum is at least 1e-30, squares that underflow change it by
+// less than 1e-13 relative. Only smaller sums are taken again in FP64.
 template <typename R>
 __device__ __forceinline__ void householder_reflector(const cplx<R>* y, int j, int m, int lane, double tiny2,
                                                       cplx<R>* vhead, cplx<R>* tau, cplx<R>* alpha) {
   double nr2 = 0.0;
-  for (int row = j + lane; row < m; row += 32) {
-    const double re = (double)y[row].re, im = (double)y[row].im;
-    nr2 = fma(re, re, fma(im, im, nr2));
+  bool done = false;
+  if constexpr (sizeof(R) == 4) {
+    float nf = 0.f;
+    for (int row = j + lane; row < m; row += 32) nf = fmaf(y[row].re, y[row].re, fmaf(y[row].im, y[row].im, nf));
+    nf = warp_sum(nf);              // the same value in every lane
+    if (nf >= 1e-30f) { nr2 = (double)nf; done = true; }
   }
-  nr2 = warp_sum(nr2);
+  if (!done) {
+    for (int row = j + lane; row < m; row += 32) {
+      const double re = (double)y[row].re, im = (double)y[row].im;
+      nr2 = fma(re, re, fma(im, im, nr2));
+    }
+    nr2 = warp_sum(nr2);
+  }
   if (lane == 0) reflector_params<R>(nr2, y[j], tiny2, vhead[j], tau[j], alpha[j]);
 }
 

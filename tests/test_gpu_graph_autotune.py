@@ -102,6 +102,9 @@ def test_small_chi_variants_agree(T):
             got = T.tepai_sample_values(ctx, prob, q)["v"]
             assert float(np.max(np.abs(got - ref))) <= TOL64, variant
         best, rate = T.tepai_autotune(ctx, prob, par, None, trial_steps=20)
-        assert best in (1, 3, 4, 6) and rate > 0.0
+        # a variant whose shape repeats an earlier one is not timed; which of
+        # 4 (128 threads) and 5 (256) repeats variant 1's default shape depends
+        # on the default rule
+        assert best in (1, 3, 4, 5, 6) and rate > 0.0
     finally:
         T.tepai_destroy(ctx)
