@@ -544,6 +544,9 @@ def test_three_site_update_untruncated_equals_statevector(n):
     r2 = R.run(prob, par, use_statevector=True)
     assert np.max(np.abs(r1["v"] - r2["v"])) < 1e-12
     assert all(st["three_site_updates"] > 0 and st["swap_updates"] == 0 for st in r1["stats"])
+    # moving the centre back after each update is a change of gauge only
+    r3 = R.run(prob, par, three_site=True, regauge=True)
+    assert np.max(np.abs(r3["v"] - r2["v"])) < 1e-12
 
 
 def test_three_site_truncation_fidelity_is_the_product_of_kept_weights():
