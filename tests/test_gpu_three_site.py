@@ -99,3 +99,21 @@ def test_chi128_three_site_staged(T, ctx, precision, tol, cutoff):
     err = np.max(np.abs(got["v"] - ref["v"]))
     print("chi 128 three-site, precision", precision, "max err", err, "max chi", got["stats"]["max_chi"])
     assert err <= tol
+
+
+def test_chi128_three_site_on_tensor_cores(T, ctx):
+    """Three-site updates on the tensor-core shape (launch variant 7): the first
+    split's projection U1^H theta3' (k1 x 512) and both splits' Jacobi run on
+    tcgen05."""
+    prob = W.spin_ring(16, 1.0, seed=5, Jz=0.5)
+    tens, dims = W.random_mps_tensors(16, 128, seed=105)
+    par = _three(W.Params(T=3.0, n_steps=18000, delta=math.pi / 1024, n_samples=2, chi_max=128,
+                          cutoff=1e-10, n_snapshots=1, seed=7, precision=1, run_steps=1, launch_variant=7))
+    got = T.tepai_sample_values(ctx, prob, par, (tens, dims))
+    _check_stats(got["stats"])
+    assert got["stats"]["tc_flops"] > 0
+    ref = oracle_run.run(prob, par, init_tensors=tens, three_site=True, **oracle_rule(par))
+    assert np.array_equal(got["sign"], ref["sign"])
+    err = np.max(np.abs(got["v"] - ref["v"]))
+    print("chi 128 three-site on tensor cores, max err", err)
+    assert err <= TOLMIX
